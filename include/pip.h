@@ -1,0 +1,266 @@
+/*
+ * pip.h - C ABI of the GB300 census-block point-in-polygon join.
+ *
+ * The operation (Kepner et al., "Fast Mapping onto Census Blocks"):
+ *   Sec. II    points are IEEE-double vectors x_pt (longitude) and y_pt
+ *              (latitude); polygons are vertex rings with bounding boxes,
+ *              organised in a hierarchy (state -> county -> block group).
+ *   Sec. III   bounding boxes, level by level, choose which polygons get the
+ *              crossing-number test (Sec. III-A: ray to +x, odd = inside;
+ *              concave and multiply-connected polygons allowed); the first
+ *              (lowest-index) containing polygon claims a point (Appendix A).
+ *   Sec. IV    cells that lie wholly inside one polygon answer without any
+ *              crossing test ("true hit filtering").
+ * The call shape follows the paper's problem statement: load a polygon set
+ * once, then map point vectors to block ids (Appendix A findCensusBlock is
+ * the query, Appendix B buildCensusStruct the load).
+ *
+ * Exact semantics used by every entry point:
+ *   Q(v)   the integer nearest to the real number v * 10^7 (ties to even);
+ *          v is valid iff it is finite and |Q(v)| <= 2^31 - 1.
+ *   edge   a->b counts for the lattice point p iff (a.y > p.y) != (b.y > p.y)
+ *          and its crossing with the line y = p.y lies strictly right of p
+ *          (decided with exact 64-bit integer orientation signs).
+ *   inside the parity of counted edges over all rings of the polygon.
+ *   id(p)  the smallest polygon index i with inside(P_i, p), else -1; an
+ *          invalid coordinate also gives -1.
+ * Polygons therefore own their left and bottom boundary: a point on a shared
+ * edge or vertex belongs to exactly one block of a gap-free partition.
+ *
+ * Conventions:
+ *   - No exceptions cross the ABI; every call returns a pip_status and
+ *     leaves a thread-local message for pip_last_error().
+ *   - `stream` arguments are cudaStream_t handles passed as void* (NULL =
+ *     the legacy default stream). Calls documented as asynchronous enqueue
+ *     work on that stream and return; the caller synchronises the stream.
+ *   - Input pointers may be host or device memory (detected with
+ *     cudaPointerGetAttributes); the library never keeps them after the
+ *     call returns (asynchronous calls read them until the stream reaches
+ *     the enqueued work). Output pointers are caller-owned.
+ *   - n = 0 is a no-op returning PIP_OK; a NULL pointer with n > 0 is
+ *     PIP_EINVAL.
+ */
+#ifndef PIP_H
+#define PIP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pip_set_s* pip_set;         /* opaque; owns device memory */
+typedef struct pip_server_s* pip_server;   /* opaque serving loop */
+typedef struct pip_plan_s* pip_plan;       /* opaque batched launch plan */
+
+typedef enum {
+  PIP_OK = 0,
+  PIP_EINVAL = 1,    /* bad argument (NULL, negative size, malformed CSR) */
+  PIP_ENOMEM = 2,    /* device or host allocation failed */
+  PIP_ECUDA = 3,     /* a CUDA runtime call failed (message has the name) */
+  PIP_ERANGE = 4,    /* an edge spans >= 2^31 lattice units, or an extent overflows */
+  PIP_ETIMEOUT = 5,  /* a bounded device or host wait ran out */
+  PIP_EBUSY = 6      /* admission refused (serving) or resource in use */
+} pip_status;
+
+/* Optional allocator hook for device memory. alloc returns a device pointer
+ * usable on `stream` (NULL on failure); free releases it in stream order.
+ * When no hook is given the library uses the CUDA stream-ordered pool. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* stream, void* ctx);
+  void (*free)(void* ptr, void* stream, void* ctx);
+  void* ctx;
+} pip_allocator;
+
+/* Index build options (Sec. IV: cells of different sizes; interior cells
+ * answer at once, boundary cells keep the crossing test). 0 = automatic. */
+typedef struct {
+  int32_t cell_log2;    /* log2 side of a top-level cell in lattice units (0 = auto) */
+  int32_t max_depth;    /* subdivision levels below the top grid; -1 = auto, 0 = uniform grid */
+  int32_t fanout_log2;  /* a split cell has 4^fanout_log2 children (0 = auto = 2) */
+  int32_t leaf_edges;   /* split a boundary cell holding more kept edges than this (0 = auto) */
+  int32_t size_ratio;   /* split while cell side * ratio > smallest candidate box side
+                           (0 = auto, negative = off) */
+  int32_t pts_per_cta;  /* residual points per crossing work item (0 = auto) */
+  int32_t stage_depth;  /* shared-memory stages in the crossing kernel, 1 or 2 (0 = auto) */
+  int32_t cand_mode;    /* 0 = auto, 1 = descend the box hierarchy, 2 = rasterize block boxes */
+} pip_build_opts;
+
+/* Facts about a loaded set's index (for tests, tuning and reports). */
+typedef struct {
+  int64_t n_poly, n_ring, n_vert, n_levels;
+  int64_t top_cells;        /* cells of the top grid */
+  int64_t table_entries;    /* descriptors: top grid + child tables */
+  int64_t leaves;           /* boundary leaf cells (keep the crossing test) */
+  int64_t interior_cells;   /* cells answered by one polygon id */
+  int64_t empty_cells;      /* cells answered by -1 */
+  int64_t superbins;        /* groups of 32 leaf slots, the binning key */
+  int64_t leaf_cands;       /* candidate polygons over all leaves */
+  int64_t leaf_edges;       /* clipped edges over all leaves */
+  int64_t index_bytes;      /* device bytes of table + leaf blobs */
+  int64_t max_blob_bytes;   /* largest per-superbin blob */
+  int32_t cell_log2, fanout_log2, depth, cand_mode;
+  int32_t pts_per_cta, stage_depth;
+  int32_t grid_x0, grid_y0; /* lattice origin of the grid */
+  int64_t grid_nx, grid_ny;
+  double build_ms;          /* device time of the last index build */
+} pip_set_info_t;
+
+/* Per-call counters of pip_project_ex (read after the stream is synchronised). */
+typedef struct {
+  int64_t n;          /* points projected */
+  int64_t residual;   /* points that fell in boundary cells (crossing tests) */
+  int64_t items;      /* crossing work items */
+} pip_project_stats;
+
+/* ---- Polygon sets (Sec. III-B data structure; Appendix B) -------------- */
+
+/* Load a polygon set given on the 1e-7 degree lattice and build its index on
+ * the device (synchronous: returns after the build finished on `stream`).
+ *   vx, vy          [n_vert] int32 vertex coordinates (host or device)
+ *   ring_off        [n_ring+1] int64: ring r is vertices [ring_off[r], ring_off[r+1]);
+ *                   each ring is closed implicitly (last -> first); a repeated
+ *                   closing vertex is allowed; orientation does not matter
+ *   poly_ring_off   [n_poly+1] int64: polygon p is rings [poly_ring_off[p], ...[p+1]);
+ *                   extra rings are holes or islands (even-odd rule)
+ *   parent          n_levels pointers; parent[0][i] is the level-1 node (tract)
+ *                   of polygon i, parent[l][j] the level-(l+1) node of level-l
+ *                   node j (tract -> county -> region). NULL / 0 = flat set.
+ *                   Parent boxes are unions of child boxes: the hierarchy only
+ *                   prunes candidates and never changes an answer.
+ *   opts, alloc     may be NULL (defaults).
+ * Errors: PIP_EINVAL (NULL with n > 0, non-monotone offsets, n_poly >= 2^30),
+ * PIP_ERANGE (an edge spans >= 2^31 units), PIP_ENOMEM, PIP_ECUDA. On error
+ * *out is NULL and nothing is leaked. */
+pip_status pip_set_load_i32(const int32_t* vx, const int32_t* vy, int64_t n_vert,
+                            const int64_t* ring_off, int64_t n_ring,
+                            const int64_t* poly_ring_off, int32_t n_poly,
+                            const int32_t* const* parent, int32_t n_levels,
+                            const pip_build_opts* opts, const pip_allocator* alloc,
+                            void* stream, pip_set* out);
+
+/* Same, with double vertex coordinates in degrees, quantized by Q on the
+ * device (a vertex with an invalid coordinate is PIP_ERANGE). */
+pip_status pip_set_load_f64(const double* vx, const double* vy, int64_t n_vert,
+                            const int64_t* ring_off, int64_t n_ring,
+                            const int64_t* poly_ring_off, int32_t n_poly,
+                            const int32_t* const* parent, int32_t n_levels,
+                            const pip_build_opts* opts, const pip_allocator* alloc,
+                            void* stream, pip_set* out);
+
+/* Rebuild the index of a loaded set with new options (synchronous). */
+pip_status pip_set_rebuild(pip_set set, const pip_build_opts* opts, void* stream);
+
+/* Index facts. */
+pip_status pip_set_info(pip_set set, pip_set_info_t* info);
+
+/* Free a set and its device memory (synchronises the device first). */
+pip_status pip_set_free(pip_set set);
+
+/* ---- Projection (Appendix A findCensusBlock; Sec. IV true-hit filter) --- */
+
+/* out[i] = id((lon[i], lat[i])) for i < n. Asynchronous on `stream` when
+ * lon, lat and out are device pointers. With host pointers the call streams
+ * the points through the device in chunks (pinned host memory overlaps the
+ * copies with compute) and returns after out[] is written.
+ * out must not alias lon or lat. n < 2^32 per call when device-resident. */
+pip_status pip_project(pip_set set, const double* lon, const double* lat, int64_t n,
+                       int32_t* out, void* stream);
+
+/* pip_project plus counters; stats (host) is filled after stream sync and
+ * may be NULL. */
+pip_status pip_project_ex(pip_set set, const double* lon, const double* lat, int64_t n,
+                          int32_t* out, void* stream, pip_project_stats* stats);
+
+/* Device error word of the set (a bounded device wait that ran out sets it):
+ * synchronises `stream`, returns PIP_OK or PIP_ETIMEOUT and clears it. */
+pip_status pip_set_check(pip_set set, void* stream);
+
+/* ---- Batched form: many queries over many sets in one launch ------------ */
+
+typedef struct {
+  pip_set set;
+  const double* lon;   /* device pointers */
+  const double* lat;
+  int64_t n;
+  int32_t* out;
+} pip_query;
+
+/* A plan holds the device buffers and a CUDA graph of one persistent,
+ * work-stealing launch (classify, bin, crossing phases separated by
+ * grid-wide barriers with bounded waits). max_points / max_queries bound
+ * what one launch may carry. */
+pip_status pip_plan_create(int64_t max_points, int32_t max_queries, void* stream,
+                           pip_plan* out);
+/* Run q[0..n_q) in one graph launch on `stream` (asynchronous). The same
+ * results as n_q separate pip_project calls, bit for bit. */
+pip_status pip_plan_run(pip_plan plan, const pip_query* q, int32_t n_q, void* stream);
+/* Synchronise `stream` and report a device timeout of the last run. */
+pip_status pip_plan_check(pip_plan plan, void* stream);
+pip_status pip_plan_destroy(pip_plan plan);
+
+/* One-shot convenience: create a plan, run, destroy (synchronous). */
+pip_status pip_project_batch(const pip_query* q, int32_t n_q, void* stream);
+
+/* Autotuner: time candidate (cell_log2, pts_per_cta, stage_depth) settings
+ * on a sample of the set's queries (device pointers) and rebuild the set
+ * with the fastest; the chosen options are written to *chosen (may be NULL). */
+pip_status pip_set_tune(pip_set set, const double* lon, const double* lat, int64_t n_sample,
+                        void* stream, pip_build_opts* chosen);
+
+/* ---- Served form: continuous batching over resident sets ---------------- */
+
+typedef struct {
+  int32_t n_streams;          /* concurrent launches in flight (0 = 2) */
+  int64_t mem_budget_bytes;   /* device bytes for in-flight requests (0 = 1/4 of free) */
+  int64_t max_batch_points;   /* points coalesced into one launch (0 = 1<<24) */
+  int32_t max_batch_queries;  /* requests coalesced into one launch (0 = 1024) */
+  int32_t max_pending;        /* queued requests before submit says PIP_EBUSY (0 = 1<<20) */
+} pip_server_opts;
+
+typedef struct {
+  int64_t submitted, completed, rejected, launches;
+  int64_t points;
+  double p50_us, p99_us, max_us, mean_batch_queries;
+} pip_server_stats_t;
+
+/* Start a serving loop over resident sets (the sets must outlive it). */
+pip_status pip_server_create(const pip_set* sets, int32_t n_sets, const pip_server_opts* opts,
+                             pip_server* out);
+/* Queue a request: lon/lat/out are host memory (pinned is fastest) that
+ * stays valid until pip_server_wait reports it done. A request that arrives
+ * while others run is admitted into the next launch as soon as a stream and
+ * device memory are free (continuous batching). */
+pip_status pip_server_submit(pip_server srv, int32_t set, const double* lon, const double* lat,
+                             int64_t n, int32_t* out, uint64_t* ticket);
+/* Wait up to timeout_us (< 0 = forever) for a ticket. PIP_ETIMEOUT if not done. */
+pip_status pip_server_wait(pip_server srv, uint64_t ticket, int64_t timeout_us);
+/* Latency percentiles of completed requests since creation or the last reset. */
+pip_status pip_server_stats(pip_server srv, pip_server_stats_t* st, int32_t reset);
+void pip_server_destroy(pip_server srv);
+
+/* ---- Diagnostics --------------------------------------------------------- */
+
+/* Q on the device for n doubles (device pointers): q[i], valid[i] (0/1).
+ * Exposes the device quantizer so tests can compare it bit for bit. */
+pip_status pip_quantize(const double* v, int64_t n, int32_t* q, uint8_t* valid, void* stream);
+
+/* Candidate polygons per top-level cell, for checking that hierarchy
+ * descent and box rasterization agree: fills off[top_cells+1] and
+ * ids[cap] (host arrays); returns PIP_EINVAL if cap is too small
+ * (off[top_cells] then holds the needed size). */
+pip_status pip_set_top_candidates(pip_set set, int32_t cand_mode, int64_t* off, int32_t* ids,
+                                  int64_t cap);
+
+/* Thread-local message of the last failing call on this thread. */
+const char* pip_last_error(void);
+
+/* ABI version: major * 10000 + minor * 100 + patch. */
+int32_t pip_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIP_H */

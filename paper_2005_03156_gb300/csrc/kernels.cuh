@@ -1,0 +1,260 @@
+// Device code of the projection path, shared by the plain and the batched
+// forms.
+//
+//   K1 classify   streams the points (two 16-byte loads of lon and two of lat
+//                 per 4 points), quantizes them with integer instructions,
+//                 walks the cell trie and writes the id of points in EMPTY
+//                 and INTERIOR cells at once (Sec. IV true-hit filtering).
+//                 Points in boundary leaves are appended to a residual queue
+//                 (warp-aggregated atomics) and counted per superbin.
+//   K2 bin        counting sort of the residual by superbin: scan of the
+//                 counts, scatter, and a list of work items of at most
+//                 pts_per_cta points (the GPU form of sorting points so many
+//                 share one polygon call, Sec. III-A / III).
+//   K3 cross      persistent CTAs take work items from an atomic counter;
+//                 each stages its superbin's record (candidates + clipped
+//                 edges) into shared memory with one cp.async.bulk copy
+//                 completed on an mbarrier (double-buffered: the next item's
+//                 copy flies while the current one is tested) and runs the
+//                 exact crossing-number test (Sec. III-A). Points whose leaf
+//                 holds a long edge list are tested by the whole warp: lanes
+//                 take strided edges and a ballot + popc gives the parity.
+#pragma once
+
+#include "pip_internal.cuh"
+
+namespace pip {
+
+constexpr int K1_THREADS = 256;
+constexpr int K3_THREADS = 256;
+constexpr int LONG_LIST = 48;  // edges above which a point is tested by its whole warp
+constexpr unsigned long long WAIT_NS = 2000000000ull;  // bounded waits: 2 s
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// --------------------------------------------------------------- K1 pieces
+// Trie walk for 4 points at once so their dependent loads overlap.
+__device__ __forceinline__ void lookup4(const IndexView& ix, const int32_t (&qx)[4],
+                                        const int32_t (&qy)[4], const bool (&ok)[4],
+                                        uint32_t (&d)[4]) {
+  uint32_t dx[4], dy[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    dx[j] = (uint32_t)qx[j] - (uint32_t)ix.gx0;
+    dy[j] = (uint32_t)qy[j] - (uint32_t)ix.gy0;
+    const uint32_t cx = dx[j] >> ix.s0, cy = dy[j] >> ix.s0;
+    const bool in = ok[j] & (cx < ix.nx) & (cy < ix.ny) & (qx[j] >= ix.gx0) & (qy[j] >= ix.gy0);
+    d[j] = in ? __ldg(ix.table + (size_t)cy * ix.nx + cx) : 0u;
+  }
+  int s = ix.s0;
+  const uint32_t m = (1u << ix.k) - 1u;
+#pragma unroll 1
+  while (((d[0] >> 30) == TAG_CHILD) | ((d[1] >> 30) == TAG_CHILD) | ((d[2] >> 30) == TAG_CHILD) |
+         ((d[3] >> 30) == TAG_CHILD)) {
+    s -= ix.k;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if ((d[j] >> 30) == TAG_CHILD) {
+        const uint32_t sub = (((dy[j] >> s) & m) << ix.k) | ((dx[j] >> s) & m);
+        d[j] = __ldg(ix.table + (d[j] & PAYLOAD_MASK) + sub);
+      }
+    }
+  }
+}
+
+// Append up to 4 residual points of this lane to the queue with one atomic
+// per warp; count them per superbin (hist may be offset per set).
+__device__ __forceinline__ void append_residual(uint32_t mask, const int32_t (&qx)[4],
+                                                const int32_t (&qy)[4], const uint32_t (&d)[4],
+                                                uint32_t idx0, Residual* __restrict__ queue,
+                                                uint32_t* __restrict__ qcount,
+                                                uint32_t* __restrict__ hist, uint32_t slot_add) {
+  const uint32_t full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  if (!__any_sync(full, mask != 0u)) return;
+  const uint32_t r = __popc(mask);
+  uint32_t incl = r;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(full, incl, o);
+    if (lane >= o) incl += t;
+  }
+  uint32_t base = 0;
+  if (lane == 31) base = atomicAdd(qcount, incl);
+  base = __shfl_sync(full, base, 31) + incl - r;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (mask & (1u << j)) {
+      const uint32_t slot = (d[j] & PAYLOAD_MASK) + slot_add;
+      queue[base++] = make_uint4((uint32_t)qx[j], (uint32_t)qy[j], idx0 + j, slot);
+      atomicAdd(hist + (slot >> SB_LOG2), 1u);
+    }
+  }
+}
+
+// Classify 4 points; returns their ids (-1 for residual ones) and the
+// residual mask.
+__device__ __forceinline__ uint32_t classify4(const IndexView& ix, const double (&x)[4],
+                                              const double (&y)[4], int32_t (&id)[4],
+                                              int32_t (&qx)[4], int32_t (&qy)[4], uint32_t (&d)[4]) {
+  bool ok[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    qx[j] = 0;
+    qy[j] = 0;
+    ok[j] = quantize_double(x[j], qx[j]) & quantize_double(y[j], qy[j]);
+  }
+  lookup4(ix, qx, qy, ok, d);
+  uint32_t mask = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const uint32_t tag = d[j] >> 30;
+    id[j] = tag == TAG_INTERIOR ? (int32_t)(d[j] & PAYLOAD_MASK) : -1;
+    mask |= (tag == TAG_LEAF ? 1u : 0u) << j;
+  }
+  return mask;
+}
+
+// --------------------------------------------------------------- K3 pieces
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Thread 0: expect `bytes` on bar and start the bulk copy global -> shared.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Bounded wait for phase `parity` of bar; false when it ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_addr(bar);
+  uint32_t done = 0;
+  asm volatile(
+      "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+      : "=r"(done)
+      : "r"(a), "r"(parity)
+      : "memory");
+  if (done) return true;
+  const unsigned long long t0 = global_ns();
+  while (true) {
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (global_ns() - t0 > WAIT_NS) return false;
+  }
+}
+
+struct BlobView {
+  const uint32_t* words;  // header, candidates, edge starts
+  const int4* edges;
+};
+
+__device__ __forceinline__ BlobView blob_view(const void* base) {
+  BlobView b;
+  b.words = (const uint32_t*)base;
+  const uint32_t nc = b.words[SB_SLOTS];
+  b.edges = (const int4*)base + ((BLOB_HEADER_WORDS + nc + nc + 1 + 3) >> 2);
+  return b;
+}
+
+// Crossing test of one point against its leaf's candidates, in id order.
+__device__ __forceinline__ int32_t test_point(const BlobView& b, uint32_t local, int32_t qx,
+                                              int32_t qy) {
+  const uint32_t nc = b.words[SB_SLOTS];
+  const uint32_t* cand = b.words + BLOB_HEADER_WORDS;
+  const uint32_t* estart = cand + nc;
+  const uint32_t c0 = b.words[local], c1 = b.words[local + 1];
+  for (uint32_t c = c0; c < c1; ++c) {
+    const uint32_t cw = cand[c];
+    uint32_t par = cw >> 31;
+    const uint32_t e1 = estart[c + 1];
+    for (uint32_t e = estart[c]; e < e1; ++e) par ^= edge_crosses(b.edges[e], qx, qy);
+    if (par) return (int32_t)(cw & 0x7FFFFFFFu);
+  }
+  return -1;
+}
+
+// The same test done by the whole warp for one point (broadcast values):
+// lanes take edges lane, lane+32, ...; the parity is the popcount of the
+// ballot of the lanes' partial parities.
+__device__ __forceinline__ int32_t test_point_warp(const BlobView& b, uint32_t local, int32_t qx,
+                                                   int32_t qy) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t nc = b.words[SB_SLOTS];
+  const uint32_t* cand = b.words + BLOB_HEADER_WORDS;
+  const uint32_t* estart = cand + nc;
+  const uint32_t c0 = b.words[local], c1 = b.words[local + 1];
+  for (uint32_t c = c0; c < c1; ++c) {
+    const uint32_t cw = cand[c];
+    uint32_t part = 0;
+    const uint32_t e1 = estart[c + 1];
+    for (uint32_t e = estart[c] + lane; e < e1; e += 32) part ^= edge_crosses(b.edges[e], qx, qy);
+    const uint32_t par = (cw >> 31) ^ (__popc(__ballot_sync(0xffffffffu, part)) & 1u);
+    if (par) return (int32_t)(cw & 0x7FFFFFFFu);
+  }
+  return -1;
+}
+
+__device__ __forceinline__ uint32_t leaf_edges(const BlobView& b, uint32_t local) {
+  const uint32_t nc = b.words[SB_SLOTS];
+  const uint32_t* estart = b.words + BLOB_HEADER_WORDS + nc;
+  return estart[b.words[local + 1]] - estart[b.words[local]];
+}
+
+// Test the residual points [first, first + count) of one work item whose
+// superbin record is `b`; writes the ids through `store`.
+template <class Store>
+__device__ __forceinline__ void test_item(const BlobView& b, const Residual* __restrict__ binned,
+                                          uint32_t first, uint32_t count, Store store) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t warp_base = (threadIdx.x & ~31u);
+  for (uint32_t base = warp_base; base < count; base += blockDim.x) {
+    const uint32_t t = base + lane;
+    const bool active = t < count;
+    Residual r = make_uint4(0, 0, 0, 0);
+    if (active) r = binned[first + t];
+    const uint32_t local = r.w & (SB_SLOTS - 1);
+    const bool is_long = active && leaf_edges(b, local) > (uint32_t)LONG_LIST;
+    int32_t id = -1;
+    if (active && !is_long) id = test_point(b, local, (int32_t)r.x, (int32_t)r.y);
+    uint32_t lm = __ballot_sync(0xffffffffu, is_long);
+    while (lm) {
+      const int j = __ffs(lm) - 1;
+      lm &= lm - 1;
+      const int32_t px = (int32_t)__shfl_sync(0xffffffffu, r.x, j);
+      const int32_t py = (int32_t)__shfl_sync(0xffffffffu, r.y, j);
+      const uint32_t lj = __shfl_sync(0xffffffffu, local, j);
+      const int32_t v = test_point_warp(b, lj, px, py);
+      if (lane == j) id = v;
+    }
+    if (active) store(r, id);
+  }
+}
+
+}  // namespace pip

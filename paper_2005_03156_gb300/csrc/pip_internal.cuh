@@ -1,0 +1,260 @@
+// Internal definitions shared by the library's translation units.
+//
+// Layout of a loaded set in HBM (all device-resident, built by index.cu):
+//   table  u32 descriptors: the top grid (row-major, nx * ny) followed by the
+//          child tables of split cells (4^k entries each). A descriptor is
+//          tag:2 | payload:30 with
+//            TAG_EMPTY     no polygon contains any point of the cell  -> -1
+//            TAG_INTERIOR  payload = polygon id answering every point
+//            TAG_LEAF      payload = leaf slot: the crossing test decides
+//            TAG_CHILD     payload = offset of the cell's child table
+//   blobs  one 16-byte-aligned record per superbin (32 consecutive leaf
+//          slots), copied to shared memory by one bulk copy:
+//            u32 leaf_start[33]     candidate range of each slot
+//            u32 cand[nc]           polygon id | base_parity << 31
+//            u32 edge_start[nc + 1] edge range of each candidate
+//            (pad to 16 bytes)
+//            int4 edge[ne]          (ax, ay, bx, by) with ay < by
+//   sbdesc uint2 per superbin: blob offset and size in 16-byte units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/pip.h"
+
+namespace pip {
+
+constexpr uint32_t TAG_EMPTY = 0u;
+constexpr uint32_t TAG_INTERIOR = 1u;
+constexpr uint32_t TAG_LEAF = 2u;
+constexpr uint32_t TAG_CHILD = 3u;
+constexpr uint32_t PAYLOAD_MASK = 0x3FFFFFFFu;
+constexpr int SB_LOG2 = 5;  // 32 leaf slots per superbin
+constexpr int SB_SLOTS = 1 << SB_LOG2;
+constexpr int BLOB_HEADER_WORDS = SB_SLOTS + 1;
+constexpr int MAX_LEVELS = 12;
+
+__host__ __device__ inline uint32_t make_desc(uint32_t tag, uint32_t payload) {
+  return (tag << 30) | (payload & PAYLOAD_MASK);
+}
+
+// Device view of one set's index, passed to kernels by value.
+struct IndexView {
+  int32_t gx0, gy0;       // lattice origin of the grid
+  uint32_t nx, ny;        // top cells per row / column
+  int32_t s0;             // log2 side of a top cell
+  int32_t k;              // log2 children per side of a split cell
+  int32_t depth;          // deepest level present
+  uint32_t n_sb;          // superbins
+  const uint32_t* table;  // descriptors
+  const uint4* blobs;     // superbin records (16-byte units)
+  const uint2* sbdesc;    // per superbin: (offset, size) in 16-byte units
+};
+
+// Residual entry: a point that fell in a boundary leaf.
+// x = qx, y = qy, z = index of the point within the call (or batch),
+// w = leaf slot (superbin = slot >> 5).
+typedef uint4 Residual;
+
+// ---------------------------------------------------------------------------
+// Q(v) on the device with integer instructions only (GB300's double rate is
+// a small fraction of its integer rate). Q(v) is the integer nearest to the
+// exact product v * 10^7 (ties to even); valid iff finite and |Q| <= 2^31-1.
+//
+// With v = m * 2^(e-1075) (m the 53-bit significand, e the biased exponent)
+// and 10^7 = 78125 * 2^7, the exact product is P * 2^(e-1068), P = m * 78125
+// < 2^70. For 1004 <= e <= 1030 (2^-19 <= |v| < 2^8) the product in 32.32
+// fixed point is P >> (1036 - e), a shift of 6..32 bits, taken with two
+// funnel shifts; the bits shifted out fold into a sticky bit for the
+// round-half-even decision. Other exponents are rare and take an exact
+// 128-bit path (tiny values) or are out of range.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool quantize_slow(uint32_t hi, uint32_t lo, int32_t& q) {
+  const uint32_t e = (hi >> 20) & 0x7FFu;
+  if (e >= 1031u) return false;  // |v| >= 2^8 (includes inf, NaN): |v*1e7| > 2^31
+  const uint64_t frac = ((uint64_t)(hi & 0xFFFFFu) << 32) | lo;
+  if (e == 0u && frac == 0u) {
+    q = 0;
+    return true;
+  }
+  // only |v| < 2^-19 reaches here (the fast path covers [2^-19, 2^8))
+  const uint64_t m = e ? (frac | (1ull << 52)) : frac;
+  const int sh = (int)(e ? 1075u - e : 1074u);  // v = m * 2^-sh, sh >= 52
+  const unsigned __int128 prod = (unsigned __int128)m * 10000000u;  // < 2^77
+  uint64_t whole;
+  unsigned __int128 rest, half;
+  if (sh >= 100) {  // prod < 2^77 < 2^99: rounds to zero
+    whole = 0;
+    rest = 0;
+    half = 1;
+  } else {
+    whole = (uint64_t)(prod >> sh);
+    rest = prod & ((((unsigned __int128)1) << sh) - 1);
+    half = ((unsigned __int128)1) << (sh - 1);
+  }
+  if (rest > half || (rest == half && (whole & 1ull))) whole += 1;
+  const int32_t w = (int32_t)whole;  // < 20 here
+  q = (hi >> 31) ? -w : w;
+  return true;
+}
+
+__device__ __forceinline__ bool quantize_bits(uint32_t hi, uint32_t lo, int32_t& q) {
+  const uint32_t e = (hi >> 20) & 0x7FFu;
+  const uint32_t sh = 1036u - e;  // wraps for e > 1036: fails the range test
+  if (sh - 6u > 26u) return quantize_slow(hi, lo, q);
+  const uint32_t mh = (hi & 0xFFFFFu) | 0x100000u;
+  const uint64_t c = (uint64_t)lo * 78125u;                       // < 2^49
+  const uint64_t a = (uint64_t)mh * 78125u + (uint32_t)(c >> 32);  // < 2^39
+  const uint32_t p0 = (uint32_t)c, p1 = (uint32_t)a, p2 = (uint32_t)(a >> 32);
+  const uint32_t t_lo = __funnelshift_rc(p0, p1, sh);  // 32.32 fixed point
+  const uint32_t t_hi = __funnelshift_rc(p1, p2, sh);
+  const uint32_t sticky = (p0 << (32u - sh)) != 0u;
+  const uint32_t f = t_lo | sticky;
+  const uint32_t mag = t_hi + (f > (0x80000000u - (t_hi & 1u)) ? 1u : 0u);
+  if (mag > 0x7FFFFFFFu) return false;
+  q = (hi >> 31) ? -(int32_t)mag : (int32_t)mag;
+  return true;
+}
+
+__device__ __forceinline__ bool quantize_double(double v, int32_t& q) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return quantize_bits((uint32_t)(b >> 32), (uint32_t)b, q);
+}
+
+// ---------------------------------------------------------------------------
+// Crossing-number contribution (Sec. III-A) of a stored edge for the lattice
+// point (px, py). Stored edges have ay < by (horizontal edges never count and
+// are not stored; the even-odd parity does not depend on edge direction).
+// The edge counts iff ay <= py < by and its crossing with y = py lies
+// strictly right of px: wholly right counts, wholly at-or-left does not, and
+// otherwise the sign of (bx-ax)(py-ay) - (by-ay)(px-ax) decides (> 0 counts).
+// The early-outs keep |px-ax| <= |bx-ax| < 2^31, so both products are exact
+// 32x32->64 bit multiplies.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int32_t sub32(int32_t a, int32_t b) {
+  return (int32_t)((uint32_t)a - (uint32_t)b);  // wraps; exact where it is used
+}
+
+__device__ __forceinline__ uint32_t edge_crosses(int4 e, int32_t px, int32_t py) {
+  const bool in_y = (py >= e.y) & (py < e.w);
+  const int32_t xmin = min(e.x, e.z), xmax = max(e.x, e.z);
+  const bool right = px < xmin;
+  const bool span = (px >= xmin) & (px < xmax);
+  const long long l = (long long)sub32(e.z, e.x) * (long long)sub32(py, e.y);
+  const long long r = (long long)sub32(e.w, e.y) * (long long)sub32(px, e.x);
+  return (uint32_t)(in_y & (right | (span & (l > r))));
+}
+
+// Trie lookup: descriptor of the leaf cell holding (qx, qy). Returns
+// TAG_EMPTY for points outside the grid.
+__device__ __forceinline__ uint32_t lookup(const IndexView& ix, int32_t qx, int32_t qy) {
+  const uint32_t dx = (uint32_t)qx - (uint32_t)ix.gx0;
+  const uint32_t dy = (uint32_t)qy - (uint32_t)ix.gy0;
+  const uint32_t cx = dx >> ix.s0, cy = dy >> ix.s0;
+  if (cx >= ix.nx || cy >= ix.ny || qx < ix.gx0 || qy < ix.gy0) return make_desc(TAG_EMPTY, 0);
+  uint32_t d = __ldg(ix.table + (size_t)cy * ix.nx + cx);
+  int s = ix.s0;
+  const uint32_t m = (1u << ix.k) - 1u;
+#pragma unroll 1
+  while ((d >> 30) == TAG_CHILD) {
+    s -= ix.k;
+    const uint32_t sub = (((dy >> s) & m) << ix.k) | ((dx >> s) & m);
+    d = __ldg(ix.table + (d & PAYLOAD_MASK) + sub);
+  }
+  return d;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side helpers
+// ---------------------------------------------------------------------------
+void set_error(const std::string& msg);
+pip_status fail(pip_status st, const std::string& msg);
+pip_status cuda_fail(cudaError_t e, const char* what);
+
+#define PIP_CUDA(call)                                        \
+  do {                                                        \
+    cudaError_t _e = (call);                                  \
+    if (_e != cudaSuccess) return ::pip::cuda_fail(_e, #call); \
+  } while (0)
+
+int num_sms();
+bool is_device_ptr(const void* p);
+
+// Device memory with an optional user allocator (stream ordered).
+struct Alloc {
+  pip_allocator hook{};
+  bool has_hook = false;
+  void* get(size_t bytes, cudaStream_t s);
+  void put(void* p, cudaStream_t s);
+};
+
+template <class T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  Alloc* a = nullptr;
+  cudaStream_t s = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  DBuf(DBuf&& o) noexcept { *this = std::move(o); }
+  DBuf& operator=(DBuf&& o) noexcept {
+    if (this != &o) {
+      release();
+      p = o.p; n = o.n; a = o.a; s = o.s;
+      o.p = nullptr; o.n = 0;
+    }
+    return *this;
+  }
+  ~DBuf() { release(); }
+  bool alloc(Alloc* al, size_t count, cudaStream_t st) {
+    release();
+    a = al;
+    s = st;
+    n = count;
+    if (count == 0) return true;
+    p = (T*)a->get(count * sizeof(T), st);
+    return p != nullptr;
+  }
+  void release() {
+    if (p && a) a->put(p, s);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+// Exclusive scan of n u32 values into u64 outputs; returns the total via
+// *total_dev (device) when not null. Stream ordered.
+pip_status scan_u32_to_u64(Alloc& al, const uint32_t* in, uint64_t* out, int64_t n,
+                           uint64_t* total_dev, cudaStream_t s);
+pip_status scan_u64(Alloc& al, const uint64_t* in, uint64_t* out, int64_t n,
+                    uint64_t* total_dev, cudaStream_t s);
+
+}  // namespace pip
+
+// The set as the library holds it.
+struct pip_set_s {
+  int device = 0;
+  pip::Alloc alloc;
+  pip_build_opts opts{};
+  // polygon data (device)
+  pip::DBuf<int32_t> vx, vy;
+  pip::DBuf<int64_t> ring_off, poly_ring_off;
+  pip::DBuf<int4> poly_box;  // (xmin, ymin, xmax, ymax); empty polygon: xmin > xmax
+  std::vector<pip::DBuf<int32_t>> parent;  // parent[l]: level-l node -> level-(l+1) node
+  std::vector<int64_t> level_len;          // nodes per level (level 0 = polygons)
+  int64_t n_vert = 0, n_ring = 0, n_poly = 0;
+  // index
+  pip::DBuf<uint32_t> table;
+  pip::DBuf<uint4> blobs;
+  pip::DBuf<uint2> sbdesc;
+  pip::IndexView view{};
+  pip_set_info_t info{};
+  // error word for bounded device waits
+  pip::DBuf<uint32_t> status;
+};

@@ -1,0 +1,383 @@
+// The plain projection path: K1 classify -> K2 bin -> K3 cross on one
+// stream, plus the chunked host-memory pipeline.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "kernels.cuh"
+
+namespace pip {
+
+// ------------------------------------------------------------------- K1
+// VEC: lon/lat are 16-byte aligned; each thread takes 4 consecutive points
+// per step (two double2 loads per coordinate, one int4 store).
+template <bool VEC>
+__global__ void __launch_bounds__(K1_THREADS) k_classify_points(
+    IndexView ix, const double* __restrict__ lon, const double* __restrict__ lat, int64_t n,
+    int32_t* __restrict__ out, Residual* __restrict__ queue, uint32_t* __restrict__ qcount,
+    uint32_t* __restrict__ hist) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t groups = (n + 3) / 4;
+  // iterate whole warps together so warp-level appends stay uniform
+  const int64_t rounds = (groups + stride - 1) / stride;
+  for (int64_t it = 0; it < rounds; ++it) {
+    const int64_t g = it * stride + tid;
+    const int64_t i0 = g * 4;
+    double x[4], y[4];
+    bool have[4];
+    if (VEC && i0 + 3 < n) {
+      const double2 a0 = __ldcs(reinterpret_cast<const double2*>(lon) + 2 * g);
+      const double2 a1 = __ldcs(reinterpret_cast<const double2*>(lon) + 2 * g + 1);
+      const double2 b0 = __ldcs(reinterpret_cast<const double2*>(lat) + 2 * g);
+      const double2 b1 = __ldcs(reinterpret_cast<const double2*>(lat) + 2 * g + 1);
+      x[0] = a0.x; x[1] = a0.y; x[2] = a1.x; x[3] = a1.y;
+      y[0] = b0.x; y[1] = b0.y; y[2] = b1.x; y[3] = b1.y;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) have[j] = true;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        have[j] = i0 + j < n;
+        x[j] = have[j] ? lon[i0 + j] : __longlong_as_double(0x7FF8000000000000ll);
+        y[j] = have[j] ? lat[i0 + j] : 0.0;
+      }
+    }
+    int32_t id[4], qx[4], qy[4];
+    uint32_t d[4];
+    uint32_t mask = classify4(ix, x, y, id, qx, qy, d);
+    if (VEC && i0 + 3 < n) {
+      __stcs(reinterpret_cast<int4*>(out) + g, make_int4(id[0], id[1], id[2], id[3]));
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (have[j]) out[i0 + j] = id[j];
+    }
+    append_residual(mask, qx, qy, d, (uint32_t)i0, queue, qcount, hist, 0u);
+  }
+}
+
+// ------------------------------------------------------------------- K2
+// packed[sb] = points << 32 | work items (ceil(points / ppc)).
+__global__ void k_pack(const uint32_t* __restrict__ hist, int64_t n_sb, uint32_t ppc,
+                       uint64_t* __restrict__ packed) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_sb;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = hist[i];
+    packed[i] = ((uint64_t)c << 32) | (uint64_t)((c + ppc - 1) / ppc);
+  }
+}
+
+__global__ void k_scatter(const Residual* __restrict__ queue, const uint32_t* __restrict__ qcount,
+                          const uint64_t* __restrict__ off, uint32_t* __restrict__ cursor,
+                          Residual* __restrict__ binned) {
+  const uint32_t n = *qcount;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const Residual e = queue[i];
+    const uint32_t sb = e.w >> SB_LOG2;
+    const uint32_t pos = (uint32_t)(off[sb] >> 32) + atomicAdd(cursor + sb, 1u);
+    binned[pos] = e;
+  }
+}
+
+// items[w] = (superbin, first point, count, 0)
+__global__ void k_items(const uint32_t* __restrict__ hist, const uint64_t* __restrict__ off,
+                        int64_t n_sb, uint32_t ppc, uint4* __restrict__ items) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_sb;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = hist[s];
+    if (!c) continue;
+    const uint32_t first = (uint32_t)(off[s] >> 32);
+    const uint32_t w0 = (uint32_t)(off[s] & 0xFFFFFFFFu);
+    for (uint32_t t = 0, w = w0; t < c; t += ppc, ++w)
+      items[w] = make_uint4((uint32_t)s, first + t, min(ppc, c - t), 0u);
+  }
+}
+
+// ------------------------------------------------------------------- K3
+struct PlainStore {
+  int32_t* out;
+  __device__ __forceinline__ void operator()(const Residual& r, int32_t id) const { out[r.z] = id; }
+};
+
+template <int STAGES>
+__global__ void __launch_bounds__(K3_THREADS) k_cross(IndexView ix, const Residual* __restrict__ binned,
+                                                      const uint4* __restrict__ items,
+                                                      const uint64_t* __restrict__ total_packed,
+                                                      uint32_t* __restrict__ item_ctr,
+                                                      int32_t* __restrict__ out,
+                                                      uint32_t* __restrict__ status,
+                                                      uint32_t stage_bytes) {
+  extern __shared__ __align__(128) uint4 stage_mem[];
+  __shared__ __align__(8) uint64_t bar[STAGES];
+  __shared__ uint32_t s_item[STAGES];
+  __shared__ uint32_t s_staged[STAGES];
+  __shared__ uint32_t s_abort;
+  const uint32_t n_items = (uint32_t)(*total_packed & 0xFFFFFFFFu);
+  const uint32_t stage16 = stage_bytes >> 4;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < STAGES; ++i) mbar_init(&bar[i], 1);
+    fence_barrier_init();
+    s_abort = 0;
+  }
+  __syncthreads();
+  uint32_t phase[STAGES];
+#pragma unroll
+  for (int i = 0; i < STAGES; ++i) phase[i] = 0;
+
+  // thread 0: claim the next item into stage st and start its copy
+  auto claim = [&](int st) {
+    const uint32_t w = atomicAdd(item_ctr, 1u);
+    s_item[st] = w;
+    s_staged[st] = 0;
+    if (w < n_items) {
+      const uint4 it = items[w];
+      const uint2 sd = ix.sbdesc[it.x];
+      if (sd.y <= stage16) {
+        fence_proxy_async();
+        bulk_load(stage_mem + (size_t)st * stage16, ix.blobs + sd.x, sd.y * 16u, &bar[st]);
+        s_staged[st] = 1;
+      }
+    }
+  };
+
+  if (threadIdx.x == 0) claim(0);
+  __syncthreads();
+  int cur = 0;
+  while (true) {
+    const uint32_t w = s_item[cur];
+    if (w >= n_items || s_abort) break;
+    if (STAGES == 2 && threadIdx.x == 0) claim(cur ^ 1);
+    const uint4 it = items[w];
+    const uint2 sd = ix.sbdesc[it.x];
+    const void* base;
+    if (s_staged[cur]) {
+      if (!mbar_wait(&bar[cur], phase[cur])) {
+        atomicOr(status, 1u);
+        s_abort = 1;
+      }
+      phase[cur] ^= 1u;
+      base = stage_mem + (size_t)cur * stage16;
+    } else {
+      base = ix.blobs + sd.x;
+    }
+    if (!s_abort) {
+      const BlobView b = blob_view(base);
+      test_item(b, binned, it.y, it.z, PlainStore{out});
+    }
+    __syncthreads();
+    if (STAGES == 2) {
+      cur ^= 1;
+    } else {
+      if (threadIdx.x == 0) claim(0);
+      __syncthreads();
+    }
+  }
+  // never leave with a copy in flight: wait (bounded) for a claimed stage
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < STAGES; ++st)
+      if (s_item[st] < n_items && s_staged[st] && st != cur) mbar_wait(&bar[st], phase[st]);
+  }
+}
+
+// ------------------------------------------------------------------- host
+static void init_pool_once() {
+  static std::once_flag f[64];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::call_once(f[dev & 63], [dev] {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+  });
+}
+
+static int k3_smem_config(int stages, uint32_t& stage_bytes) {
+  stage_bytes = stages == 2 ? 48u * 1024u : 96u * 1024u;
+  return (int)(stage_bytes * stages);
+}
+
+static pip_status k3_launch(const IndexView& ix, int stages, const Residual* binned,
+                            const uint4* items, const uint64_t* total_packed, uint32_t* item_ctr,
+                            int32_t* out, uint32_t* status, cudaStream_t s) {
+  uint32_t stage_bytes = 0;
+  const int smem = k3_smem_config(stages, stage_bytes);
+  static bool attr_set[3] = {false, false, false};
+  if (!attr_set[stages]) {
+    if (stages == 2)
+      PIP_CUDA(cudaFuncSetAttribute(k_cross<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    else
+      PIP_CUDA(cudaFuncSetAttribute(k_cross<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    attr_set[stages] = true;
+  }
+  const int ctas_per_sm = std::max(1, (int)((200 * 1024) / (smem + 2048)));
+  const unsigned grid = (unsigned)(num_sms() * std::min(ctas_per_sm, 4));
+  if (stages == 2)
+    k_cross<2><<<grid, K3_THREADS, smem, s>>>(ix, binned, items, total_packed, item_ctr, out, status,
+                                              stage_bytes);
+  else
+    k_cross<1><<<grid, K3_THREADS, smem, s>>>(ix, binned, items, total_packed, item_ctr, out, status,
+                                              stage_bytes);
+  PIP_CUDA(cudaGetLastError());
+  return PIP_OK;
+}
+
+pip_status k3_launch_public(const IndexView& ix, int stages, const Residual* binned, const uint4* items,
+                            const uint64_t* total_packed, uint32_t* item_ctr, int32_t* out,
+                            uint32_t* status, cudaStream_t s) {
+  return k3_launch(ix, stages, binned, items, total_packed, item_ctr, out, status, s);
+}
+
+// Scratch of one device-resident projection of n points.
+struct ProjScratch {
+  DBuf<Residual> queue, binned;
+  DBuf<uint32_t> hist;   // [n_sb] counts then [n_sb] cursors
+  DBuf<uint64_t> packed; // [n_sb] packed counts then [n_sb] offsets then [1] total
+  DBuf<uint4> items;
+  DBuf<uint32_t> ctr;    // [0] queue count, [1] item counter
+};
+
+pip_status project_device(pip_set_s* S, const double* lon, const double* lat, int64_t n, int32_t* out,
+                          cudaStream_t s, pip_project_stats* stats) {
+  if (n <= 0) return PIP_OK;
+  if (n >= (1ll << 32) - 1) return fail(PIP_EINVAL, "pip_project: n must be < 2^32 - 1 per device call");
+  init_pool_once();
+  Alloc* al = &S->alloc;
+  const IndexView& ix = S->view;
+  const int64_t n_sb = std::max<int64_t>(1, ix.n_sb);
+  const uint32_t ppc = (uint32_t)std::max(1, S->opts.pts_per_cta);
+  const int64_t max_items = std::min<int64_t>(n, n_sb) + n / ppc + 1;
+  ProjScratch w;
+  if (!w.queue.alloc(al, n, s) || !w.binned.alloc(al, n, s) || !w.hist.alloc(al, 2 * n_sb, s) ||
+      !w.packed.alloc(al, 2 * n_sb + 1, s) || !w.items.alloc(al, max_items, s) || !w.ctr.alloc(al, 4, s))
+    return fail(PIP_ENOMEM, "pip_project: scratch allocation failed");
+  uint32_t* hist = w.hist.p;
+  uint32_t* cursor = w.hist.p + n_sb;
+  uint64_t* packed = w.packed.p;
+  uint64_t* off = w.packed.p + n_sb;
+  uint64_t* total = w.packed.p + 2 * n_sb;
+  PIP_CUDA(cudaMemsetAsync(w.hist.p, 0, 2 * n_sb * sizeof(uint32_t), s));
+  PIP_CUDA(cudaMemsetAsync(w.ctr.p, 0, 4 * sizeof(uint32_t), s));
+  const bool vec = ((uintptr_t)lon % 16 == 0) && ((uintptr_t)lat % 16 == 0) && ((uintptr_t)out % 16 == 0);
+  const int64_t groups = (n + 3) / 4;
+  const unsigned g1 = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>((groups + K1_THREADS - 1) / K1_THREADS, (int64_t)num_sms() * 8));
+  if (vec)
+    k_classify_points<true><<<g1, K1_THREADS, 0, s>>>(ix, lon, lat, n, out, w.queue.p, w.ctr.p, hist);
+  else
+    k_classify_points<false><<<g1, K1_THREADS, 0, s>>>(ix, lon, lat, n, out, w.queue.p, w.ctr.p, hist);
+  PIP_CUDA(cudaGetLastError());
+  const unsigned gs = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_sb + 255) / 256, num_sms() * 8));
+  k_pack<<<gs, 256, 0, s>>>(hist, n_sb, ppc, packed);
+  PIP_CUDA(cudaGetLastError());
+  pip_status st = scan_u64(*al, packed, off, n_sb, total, s);
+  if (st != PIP_OK) return st;
+  k_scatter<<<(unsigned)(num_sms() * 8), 256, 0, s>>>(w.queue.p, w.ctr.p, off, cursor, w.binned.p);
+  PIP_CUDA(cudaGetLastError());
+  k_items<<<gs, 256, 0, s>>>(hist, off, n_sb, ppc, w.items.p);
+  PIP_CUDA(cudaGetLastError());
+  st = k3_launch(ix, S->opts.stage_depth, w.binned.p, w.items.p, total, w.ctr.p + 1, out, S->status.p, s);
+  if (st != PIP_OK) return st;
+  if (stats) {
+    uint32_t c[2];
+    uint64_t t = 0;
+    PIP_CUDA(cudaMemcpyAsync(c, w.ctr.p, sizeof(c), cudaMemcpyDeviceToHost, s));
+    PIP_CUDA(cudaMemcpyAsync(&t, total, sizeof(t), cudaMemcpyDeviceToHost, s));
+    PIP_CUDA(cudaStreamSynchronize(s));
+    stats->n = n;
+    stats->residual = c[0];
+    stats->items = (int64_t)(t & 0xFFFFFFFFu);
+  }
+  return PIP_OK;
+}
+
+// Host-memory inputs/outputs: stream fixed-size chunks through two device
+// buffers on two streams so one chunk's copies overlap the other's compute.
+pip_status project_host(pip_set_s* S, const double* lon, const double* lat, int64_t n, int32_t* out,
+                        cudaStream_t s, pip_project_stats* stats) {
+  const int64_t CH = 1ll << 24;
+  const int64_t chunk = std::min<int64_t>(CH, n);
+  Alloc* al = &S->alloc;
+  cudaStream_t st[2] = {s, nullptr};
+  PIP_CUDA(cudaStreamCreateWithFlags(&st[1], cudaStreamNonBlocking));
+  struct Buf {
+    DBuf<double> x, y;
+    DBuf<int32_t> o;
+  } buf[2];
+  pip_status res = PIP_OK;
+  cudaEvent_t start_ev;
+  cudaEventCreateWithFlags(&start_ev, cudaEventDisableTiming);
+  cudaEventRecord(start_ev, s);
+  cudaStreamWaitEvent(st[1], start_ev, 0);
+  for (int b = 0; b < 2 && res == PIP_OK; ++b) {
+    if (!buf[b].x.alloc(al, chunk, st[b]) || !buf[b].y.alloc(al, chunk, st[b]) ||
+        !buf[b].o.alloc(al, chunk, st[b]))
+      res = fail(PIP_ENOMEM, "pip_project: staging buffers");
+  }
+  int64_t residual = 0, items = 0;
+  for (int64_t a = 0, i = 0; a < n && res == PIP_OK; a += chunk, ++i) {
+    const int b = (int)(i & 1);
+    const int64_t c = std::min(chunk, n - a);
+    cudaError_t e = cudaMemcpyAsync(buf[b].x.p, lon + a, c * sizeof(double), cudaMemcpyDefault, st[b]);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(buf[b].y.p, lat + a, c * sizeof(double), cudaMemcpyDefault, st[b]);
+    if (e != cudaSuccess) {
+      res = cuda_fail(e, "pip_project: host-to-device copy");
+      break;
+    }
+    pip_project_stats ps{};
+    res = project_device(S, buf[b].x.p, buf[b].y.p, c, buf[b].o.p, st[b], stats ? &ps : nullptr);
+    if (res != PIP_OK) break;
+    residual += ps.residual;
+    items += ps.items;
+    e = cudaMemcpyAsync(out + a, buf[b].o.p, c * sizeof(int32_t), cudaMemcpyDefault, st[b]);
+    if (e != cudaSuccess) res = cuda_fail(e, "pip_project: device-to-host copy");
+  }
+  for (int b = 0; b < 2; ++b) {
+    buf[b].x.release();
+    buf[b].y.release();
+    buf[b].o.release();
+  }
+  cudaError_t e0 = cudaStreamSynchronize(st[1]);
+  cudaError_t e1 = cudaStreamSynchronize(st[0]);
+  cudaStreamDestroy(st[1]);
+  cudaEventDestroy(start_ev);
+  if (res == PIP_OK && e0 != cudaSuccess) res = cuda_fail(e0, "pip_project: stream");
+  if (res == PIP_OK && e1 != cudaSuccess) res = cuda_fail(e1, "pip_project: stream");
+  if (stats && res == PIP_OK) {
+    stats->n = n;
+    stats->residual = residual;
+    stats->items = items;
+  }
+  return res;
+}
+
+}  // namespace pip
+
+using namespace pip;
+
+extern "C" pip_status pip_project_ex(pip_set set, const double* lon, const double* lat, int64_t n,
+                                     int32_t* out, void* stream, pip_project_stats* stats) {
+  if (!set) return fail(PIP_EINVAL, "pip_project: NULL set");
+  if (n < 0) return fail(PIP_EINVAL, "pip_project: n < 0");
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (n == 0) return PIP_OK;
+  if (!lon || !lat || !out) return fail(PIP_EINVAL, "pip_project: NULL pointer with n > 0");
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cur != set->device) PIP_CUDA(cudaSetDevice(set->device));
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool dev = is_device_ptr(lon) && is_device_ptr(lat) && is_device_ptr(out);
+  pip_status st = dev ? project_device(set, lon, lat, n, out, s, stats)
+                      : project_host(set, lon, lat, n, out, s, stats);
+  if (cur != set->device) cudaSetDevice(cur);
+  return st;
+}
+
+extern "C" pip_status pip_project(pip_set set, const double* lon, const double* lat, int64_t n,
+                                  int32_t* out, void* stream) {
+  return pip_project_ex(set, lon, lat, n, out, stream, nullptr);
+}

@@ -1,0 +1,233 @@
+"""GPU parity of the plain projection path against the CPU oracle.
+
+Ids are integers, so the bar is bit-exact equality with the oracle (O1,
+itself pinned to O0 and to the paper in test_oracle_pins.py) on every case.
+All calls go through the C ABI (libpip.so via the Python binding).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from synth import configs, degenerate_lattice, lattice_to_degrees
+from tests import oracle_pins as pins
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pipm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2005_03156_gb300 as pipm
+    from paper_2005_03156_gb300 import build
+    build.build()
+    pipm.lib()
+    return pipm
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def project(pipm, s, lon, lat):
+    out = pipm.pip_project(s, dev(lon), dev(lat))
+    pipm.pip_set_check(s)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def test_device_quantizer_matches_oracle(pipm):
+    v = pins.q_cases(np.random.default_rng(7))
+    q, ok = pipm.pip_quantize(dev(v))
+    torch.cuda.synchronize()
+    oq, ook = oracle.quantize(v)
+    ok = ok.cpu().numpy().astype(bool)
+    q = q.cpu().numpy()
+    assert (ok == ook).all()
+    assert (q[ok] == oq[ok]).all()
+
+
+def test_tiny_full_config(pipm, tiny_set):
+    s = pipm.load_polygon_set(tiny_set)
+    lon, lat = configs.tiny_points(tiny_set)
+    got = project(pipm, s, lon, lat)
+    want = oracle.join_hier(tiny_set, lon, lat)
+    assert (got == want).all(), int((got != want).sum())
+    info = s.info()
+    assert info["leaves"] > 0 and info["interior_cells"] > 0
+
+
+def test_degenerate_points(pipm, tiny_set):
+    s = pipm.load_polygon_set(tiny_set)
+    qx, qy = degenerate_lattice(tiny_set, 200_000, np.random.default_rng(21))
+    lon, lat = lattice_to_degrees(qx), lattice_to_degrees(qy)
+    got = project(pipm, s, lon, lat)
+    want = oracle.join_hier(tiny_set, lon, lat)
+    assert (got == want).all(), int((got != want).sum())
+
+
+def test_holes_and_islands(pipm, tiny_set_holes):
+    ps = tiny_set_holes
+    s = pipm.load_polygon_set(ps)
+    qx, qy = degenerate_lattice(ps, 100_000, np.random.default_rng(22))
+    lon, lat = lattice_to_degrees(qx), lattice_to_degrees(qy)
+    lon2, lat2 = configs.tiny_points(ps, n=200_000, seed=23)
+    lon, lat = np.concatenate([lon, lon2]), np.concatenate([lat, lat2])
+    got = project(pipm, s, lon, lat)
+    want = oracle.join_hier(ps, lon, lat)
+    assert (got == want).all(), int((got != want).sum())
+
+
+OPTION_CASES = [
+    dict(max_depth=0),                                   # uniform grid
+    dict(max_depth=0, cell_log2=14),                     # fine uniform grid
+    dict(max_depth=0, cell_log2=22),                     # one coarse cell
+    dict(fanout_log2=1, leaf_edges=2, size_ratio=64),    # deep quadtree
+    dict(fanout_log2=3, leaf_edges=4),                   # fanout 64
+    dict(stage_depth=1, pts_per_cta=7),                  # single stage, tiny items
+    dict(stage_depth=2, pts_per_cta=1000),               # items larger than the CTA
+    dict(cand_mode=2),                                   # box rasterization
+    dict(cand_mode=1, size_ratio=-1, leaf_edges=1000),   # few splits, long lists (warp ballots)
+]
+
+
+@pytest.mark.parametrize("opts", OPTION_CASES, ids=[str(o) for o in OPTION_CASES])
+def test_build_options(pipm, tiny_set_holes, opts):
+    ps = tiny_set_holes
+    s = pipm.load_polygon_set(ps, opts=opts)
+    qx, qy = degenerate_lattice(ps, 60_000, np.random.default_rng(24))
+    lon, lat = lattice_to_degrees(qx), lattice_to_degrees(qy)
+    lon2, lat2 = configs.tiny_points(ps, n=100_000, seed=25)
+    lon, lat = np.concatenate([lon, lon2]), np.concatenate([lat, lat2])
+    got = project(pipm, s, lon, lat)
+    want = oracle.join_hier(ps, lon, lat)
+    assert (got == want).all(), (opts, int((got != want).sum()))
+
+
+def test_hierarchy_descent_equals_rasterization(pipm, tiny_set):
+    s = pipm.load_polygon_set(tiny_set)
+    o1, i1 = pipm.pip_set_top_candidates(s, 1)
+    o2, i2 = pipm.pip_set_top_candidates(s, 2)
+    assert (o1 == o2).all() and (i1 == i2).all()
+    # brute force: polygons whose closed box meets each cell's closed rect
+    info = s.info()
+    sh, x0, y0, nx = info["cell_log2"], info["grid_x0"], info["grid_y0"], info["grid_nx"]
+    v = tiny_set.ring_off[tiny_set.poly_ring_off]
+    for p in np.random.default_rng(3).choice(tiny_set.n_poly, 50, replace=False):
+        xs, ys = tiny_set.vx[v[p]:v[p + 1]], tiny_set.vy[v[p]:v[p + 1]]
+        cx0, cx1 = (xs.min() - x0) >> sh, (xs.max() - x0) >> sh
+        cy0, cy1 = (ys.min() - y0) >> sh, (ys.max() - y0) >> sh
+        for cy in range(cy0, cy1 + 1):
+            for cx in range(cx0, cx1 + 1):
+                c = cy * nx + cx
+                assert p in i1[o1[c]:o1[c + 1]]
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 4, 5, 31, 33, 1023, 1025, 4097])
+def test_ragged_sizes(pipm, tiny_set, n):
+    s = pipm.load_polygon_set(tiny_set)
+    lon, lat = configs.tiny_points(tiny_set, n=max(n, 1), seed=30 + n)
+    lon, lat = lon[:n], lat[:n]
+    got = project(pipm, s, lon, lat) if n else np.zeros(0, np.int32)
+    want = oracle.join_hier(tiny_set, lon, lat)
+    assert (got == want).all()
+
+
+def test_unaligned_pointers_take_scalar_path(pipm, tiny_set):
+    s = pipm.load_polygon_set(tiny_set)
+    lon, lat = configs.tiny_points(tiny_set, n=10_001, seed=40)
+    dl, da = dev(lon), dev(lat)
+    out = torch.empty(10_001, dtype=torch.int32, device="cuda")
+    got = pipm.pip_project(s, dl[1:], da[1:], out[1:])
+    torch.cuda.synchronize()
+    want = oracle.join_hier(tiny_set, lon[1:], lat[1:])
+    assert (out[1:].cpu().numpy() == want).all()
+    del got
+
+
+def test_host_pointer_streaming(pipm, tiny_set):
+    s = pipm.load_polygon_set(tiny_set)
+    lon, lat = configs.tiny_points(tiny_set, n=300_000, seed=41)
+    got = pipm.pip_project(s, lon, lat)              # numpy in/out -> chunked pipeline
+    want = oracle.join_hier(tiny_set, lon, lat)
+    assert (got == want).all()
+    lon_p = torch.from_numpy(lon).pin_memory()
+    lat_p = torch.from_numpy(lat).pin_memory()
+    out_p = torch.empty(len(lon), dtype=torch.int32).pin_memory()
+    pipm.pip_project(s, lon_p, lat_p, out_p)
+    assert (out_p.numpy() == want).all()
+
+
+def test_invalid_coordinates(pipm, tiny_set):
+    s = pipm.load_polygon_set(tiny_set)
+    bad = np.array([np.nan, np.inf, -np.inf, 1e300, 215.0, -215.0, 0.5, 0.5], np.float64)
+    ok = np.array([0.5, 0.5, 0.5, 0.5, 0.5, 0.5, np.nan, 214.7483648], np.float64)
+    got = project(pipm, s, bad, ok)
+    assert (got == -1).all()
+    got = project(pipm, s, ok[:6], bad[:6])
+    assert (got == -1).all()
+
+
+def test_overlapping_polygons_lowest_id(pipm):
+    a = [[(0, 0), (600, 0), (600, 600), (0, 600)]]
+    b = [[(300, 300), (900, 300), (900, 900), (300, 900)]]
+    c = [[(100, 100), (200, 100), (200, 200), (100, 200)]]
+    ps = pins.poly_set([b, a, c])
+    s = pipm.pip_set_load_i32(ps.vx, ps.vy, ps.ring_off, ps.poly_ring_off, opts=dict(cell_log2=6))
+    X, Y = np.meshgrid(np.arange(-5, 910, 3), np.arange(-5, 910, 3), indexing="ij")
+    lon, lat = lattice_to_degrees(X.ravel()), lattice_to_degrees(Y.ravel())
+    got = project(pipm, s, lon, lat)
+    want = oracle.join_hier(ps, lon, lat)
+    assert (got == want).all()
+
+
+def test_f64_vertex_load(pipm, tiny_set):
+    s = pipm.pip_set_load_f64(lattice_to_degrees(tiny_set.vx), lattice_to_degrees(tiny_set.vy),
+                              tiny_set.ring_off, tiny_set.poly_ring_off, parents=tiny_set.parents)
+    lon, lat = configs.tiny_points(tiny_set, n=100_000, seed=42)
+    assert (project(pipm, s, lon, lat) == oracle.join_hier(tiny_set, lon, lat)).all()
+
+
+def test_load_errors(pipm):
+    PipError = pipm.PipError
+    ps = pins.poly_set([[[(0, 0), (10, 0), (10, 10)]]])
+    with pytest.raises(PipError) as e:
+        pipm.pip_set_load_i32(ps.vx, ps.vy, np.array([0, 2], np.int64), ps.poly_ring_off)
+    assert e.value.status == 1
+    big = pins.poly_set([[[(-2**31 + 5, 0), (2**31 - 5, 0), (0, 10)]]])
+    with pytest.raises(PipError) as e:
+        pipm.pip_set_load_i32(big.vx, big.vy, big.ring_off, big.poly_ring_off)
+    assert e.value.status == 4
+    with pytest.raises(PipError) as e:
+        pipm.pip_set_load_i32(ps.vx, ps.vy, ps.ring_off, ps.poly_ring_off,
+                              parents=[np.array([-1], np.int32)])
+    assert e.value.status == 1
+
+
+def test_rebuild_keeps_results(pipm, tiny_set):
+    s = pipm.load_polygon_set(tiny_set)
+    lon, lat = configs.tiny_points(tiny_set, n=100_000, seed=43)
+    a = project(pipm, s, lon, lat)
+    pipm.pip_set_rebuild(s, dict(cell_log2=15, max_depth=1))
+    b = project(pipm, s, lon, lat)
+    assert (a == b).all()
+
+
+@pytest.mark.slow
+def test_state_scale_sampled(pipm):
+    """Full state-scale set and 1e8 points in the bench's launch shape;
+    a random sample of outputs is checked against the oracle point by point,
+    and every output is a valid id."""
+    ps = configs.state_set()
+    s = pipm.load_polygon_set(ps)
+    lon, lat = configs.state_points()
+    dlon, dlat = dev(lon), dev(lat)
+    out = pipm.pip_project(s, dlon, dlat)
+    pipm.pip_set_check(s)
+    got = out.cpu().numpy()
+    assert got.min() >= -1 and got.max() < ps.n_poly
+    idx = np.random.default_rng(44).choice(len(lon), 200_000, replace=False)
+    want = oracle.join_hier(ps, lon[idx], lat[idx])
+    assert (got[idx] == want).all(), int((got[idx] != want).sum())
