@@ -692,7 +692,7 @@ static pip_status build_hierarchy(pip_set_s* S, Alloc* al, cudaStream_t s, HierB
     k_count_children<<<blocks_for(n_ch), TB, 0, s>>>(S->parent[l - 1].p, n_ch, cnt.p, n_par, err.p);
     CHECK(scan_u32_to_u64(*al, cnt.p, hb.coff[l].p, n_par + 1, nullptr, s));
     k_fill_children<<<blocks_for(n_ch), TB, 0, s>>>(S->parent[l - 1].p, n_ch, hb.coff[l].p, cur.p,
-                                                    hb.cids[l].p, hb.box[l].p, hb.box[l - 1].p, n_par);
+                                                    hb.cids[l].p, hb.box[l].p, h.box[l - 1], n_par);
     PIP_CUDA(cudaGetLastError());
     h.box[l] = hb.box[l].p;
     h.coff[l] = hb.coff[l].p;
