@@ -253,6 +253,19 @@ pip_status pip_quantize(const double* v, int64_t n, int32_t* q, uint8_t* valid, 
 pip_status pip_set_top_candidates(pip_set set, int32_t cand_mode, int64_t* off, int32_t* ids,
                                   int64_t cap);
 
+/* Per-stage device timing of pip_project on a set, taken with CUDA events
+ * recorded on the call's stream around the stages (no synchronisation in
+ * the calls themselves). enable = capacity in calls (0 disables and frees).
+ * pip_profile_read synchronises the device and returns, for up to *n calls
+ * recorded since enabling (or the last read), the milliseconds of
+ * classify (K1), bin (K2: scan, scatter, work items) and cross (K3), each
+ * array of length *n; *n is updated to the number returned. */
+pip_status pip_profile_enable(pip_set set, int32_t capacity);
+pip_status pip_profile_read(pip_set set, double* k1_ms, double* bin_ms, double* k3_ms, int32_t* n);
+
+/* Kernel launches the library has issued in this process so far. */
+int64_t pip_kernel_launches(void);
+
 /* Thread-local message of the last failing call on this thread. */
 const char* pip_last_error(void);
 

@@ -287,3 +287,22 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def pip_profile_enable(s: PolygonSet, capacity: int):
+    _native.check(lib().pip_profile_enable(s.handle, int(capacity)))
+
+
+def pip_profile_read(s: PolygonSet, capacity: int):
+    """Per-call stage times (ms) recorded since enabling: dict of arrays."""
+    k1 = np.zeros(max(1, capacity))
+    bn = np.zeros(max(1, capacity))
+    k3 = np.zeros(max(1, capacity))
+    n = ctypes.c_int32(int(capacity))
+    _native.check(lib().pip_profile_read(s.handle, _ptr(k1), _ptr(bn), _ptr(k3), ctypes.byref(n)))
+    m = n.value
+    return {"k1_ms": k1[:m], "bin_ms": bn[:m], "k3_ms": k3[:m]}
+
+
+def pip_kernel_launches() -> int:
+    return int(lib().pip_kernel_launches())

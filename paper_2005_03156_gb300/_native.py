@@ -89,6 +89,9 @@ SIGNATURES = {
     "pip_server_destroy": (None, [P]),
     "pip_quantize": (I32, [P, I64, P, P, P]),
     "pip_set_top_candidates": (I32, [P, I32, P, P, I64]),
+    "pip_profile_enable": (I32, [P, I32]),
+    "pip_profile_read": (I32, [P, P, P, P, P]),
+    "pip_kernel_launches": (I64, []),
     "pip_last_error": (ctypes.c_char_p, []),
     "pip_version": (I32, []),
 }

@@ -1,6 +1,7 @@
 // Error plumbing, device memory, exclusive scans and the diagnostic
 // quantizer entry point.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <mutex>
 #include <string>
@@ -10,6 +11,9 @@
 namespace pip {
 
 static thread_local std::string g_last_error;
+static std::atomic<int64_t> g_launches{0};
+
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
@@ -148,6 +152,7 @@ static pip_status scan_impl(Alloc& al, const In* in, uint64_t* out, int64_t n, u
   if (blocks == 1) {
     k_block_scan<In><<<1, SCAN_THREADS, 0, s>>>(in, out, n, nullptr, total_dev);
     PIP_CUDA(cudaGetLastError());
+    count_launches(1);
     return PIP_OK;
   }
   DBuf<uint64_t> sums, offs;
@@ -159,6 +164,7 @@ static pip_status scan_impl(Alloc& al, const In* in, uint64_t* out, int64_t n, u
   if (st != PIP_OK) return st;
   k_block_scan<In><<<(unsigned)blocks, SCAN_THREADS, 0, s>>>(in, out, n, offs.p, total_dev);
   PIP_CUDA(cudaGetLastError());
+  count_launches(2);
   return PIP_OK;
 }
 
@@ -190,6 +196,8 @@ using namespace pip;
 extern "C" const char* pip_last_error(void) { return g_last_error.c_str(); }
 
 extern "C" int32_t pip_version(void) { return 10000; }
+
+extern "C" int64_t pip_kernel_launches(void) { return g_launches.load(); }
 
 extern "C" pip_status pip_quantize(const double* v, int64_t n, int32_t* q, uint8_t* valid,
                                    void* stream) {

@@ -183,6 +183,7 @@ pip_status cuda_fail(cudaError_t e, const char* what);
   } while (0)
 
 int num_sms();
+void count_launches(int64_t n);
 bool is_device_ptr(const void* p);
 
 // Device memory with an optional user allocator (stream ordered).
@@ -257,4 +258,10 @@ struct pip_set_s {
   pip_set_info_t info{};
   // error word for bounded device waits
   pip::DBuf<uint32_t> status;
+  // per-stage profiling: 4 events per recorded call
+  std::vector<cudaEvent_t> prof_ev;
+  int32_t prof_cap = 0, prof_n = 0;
+  ~pip_set_s() {
+    for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
+  }
 };

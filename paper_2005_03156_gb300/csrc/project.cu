@@ -259,6 +259,11 @@ pip_status project_device(pip_set_s* S, const double* lon, const double* lat, in
   uint64_t* packed = w.packed.p;
   uint64_t* off = w.packed.p + n_sb;
   uint64_t* total = w.packed.p + 2 * n_sb;
+  int prof = -1;
+  if (S->prof_cap > 0 && S->prof_n < S->prof_cap) {
+    prof = S->prof_n++;
+    PIP_CUDA(cudaEventRecord(S->prof_ev[4 * prof + 0], s));
+  }
   PIP_CUDA(cudaMemsetAsync(w.hist.p, 0, 2 * n_sb * sizeof(uint32_t), s));
   PIP_CUDA(cudaMemsetAsync(w.ctr.p, 0, 4 * sizeof(uint32_t), s));
   const bool vec = ((uintptr_t)lon % 16 == 0) && ((uintptr_t)lat % 16 == 0) && ((uintptr_t)out % 16 == 0);
@@ -270,6 +275,7 @@ pip_status project_device(pip_set_s* S, const double* lon, const double* lat, in
   else
     k_classify_points<false><<<g1, K1_THREADS, 0, s>>>(ix, lon, lat, n, out, w.queue.p, w.ctr.p, hist);
   PIP_CUDA(cudaGetLastError());
+  if (prof >= 0) PIP_CUDA(cudaEventRecord(S->prof_ev[4 * prof + 1], s));
   const unsigned gs = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_sb + 255) / 256, num_sms() * 8));
   k_pack<<<gs, 256, 0, s>>>(hist, n_sb, ppc, packed);
   PIP_CUDA(cudaGetLastError());
@@ -279,8 +285,11 @@ pip_status project_device(pip_set_s* S, const double* lon, const double* lat, in
   PIP_CUDA(cudaGetLastError());
   k_items<<<gs, 256, 0, s>>>(hist, off, n_sb, ppc, w.items.p);
   PIP_CUDA(cudaGetLastError());
+  if (prof >= 0) PIP_CUDA(cudaEventRecord(S->prof_ev[4 * prof + 2], s));
   st = k3_launch(ix, S->opts.stage_depth, w.binned.p, w.items.p, total, w.ctr.p + 1, out, S->status.p, s);
   if (st != PIP_OK) return st;
+  if (prof >= 0) PIP_CUDA(cudaEventRecord(S->prof_ev[4 * prof + 3], s));
+  count_launches(5);  // K1, pack, scatter, items, K3 (scans count their own)
   if (stats) {
     uint32_t c[2];
     uint64_t t = 0;

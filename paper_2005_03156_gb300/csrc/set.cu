@@ -178,3 +178,38 @@ extern "C" pip_status pip_set_top_candidates(pip_set set, int32_t cand_mode, int
   pip_status st = top_candidates_export(set, cand_mode, off, ids, cap, 0);
   return st;
 }
+
+extern "C" pip_status pip_profile_enable(pip_set set, int32_t capacity) {
+  if (!set || capacity < 0) return fail(PIP_EINVAL, "pip_profile_enable: bad argument");
+  cudaDeviceSynchronize();
+  for (cudaEvent_t e : set->prof_ev) cudaEventDestroy(e);
+  set->prof_ev.clear();
+  set->prof_cap = 0;
+  set->prof_n = 0;
+  for (int32_t i = 0; i < 4 * capacity; ++i) {
+    cudaEvent_t e;
+    PIP_CUDA(cudaEventCreate(&e));
+    set->prof_ev.push_back(e);
+  }
+  set->prof_cap = capacity;
+  return PIP_OK;
+}
+
+extern "C" pip_status pip_profile_read(pip_set set, double* k1_ms, double* bin_ms, double* k3_ms,
+                                       int32_t* n) {
+  if (!set || !n || *n < 0) return fail(PIP_EINVAL, "pip_profile_read: bad argument");
+  PIP_CUDA(cudaDeviceSynchronize());
+  const int32_t m = std::min(*n, set->prof_n);
+  for (int32_t i = 0; i < m; ++i) {
+    float a = 0, b = 0, c = 0;
+    PIP_CUDA(cudaEventElapsedTime(&a, set->prof_ev[4 * i + 0], set->prof_ev[4 * i + 1]));
+    PIP_CUDA(cudaEventElapsedTime(&b, set->prof_ev[4 * i + 1], set->prof_ev[4 * i + 2]));
+    PIP_CUDA(cudaEventElapsedTime(&c, set->prof_ev[4 * i + 2], set->prof_ev[4 * i + 3]));
+    if (k1_ms) k1_ms[i] = a;
+    if (bin_ms) bin_ms[i] = b;
+    if (k3_ms) k3_ms[i] = c;
+  }
+  *n = m;
+  set->prof_n = 0;
+  return PIP_OK;
+}
