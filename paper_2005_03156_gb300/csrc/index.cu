@@ -650,7 +650,8 @@ static void resolve_opts(const pip_build_opts& in, int64_t n_poly, long long w, 
     o.cell_log2 = std::max(4, std::min(30, s));
   }
   if (o.fanout_log2 <= 0) o.fanout_log2 = 2;
-  if (o.max_depth < 0) o.max_depth = std::max(0, std::min(8, (o.cell_log2 - 6) / o.fanout_log2));
+  if (o.max_depth == 0) o.max_depth = std::max(0, std::min(8, (o.cell_log2 - 6) / o.fanout_log2));
+  else if (o.max_depth < 0) o.max_depth = 0;  // uniform grid
   o.max_depth = std::min(o.max_depth, std::max(0, (o.cell_log2 - 1) / o.fanout_log2));
   if (o.leaf_edges <= 0) o.leaf_edges = 16;
   if (o.size_ratio == 0) o.size_ratio = 16;

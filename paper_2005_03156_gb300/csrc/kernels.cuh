@@ -8,17 +8,19 @@
 //                 Points in boundary leaves are appended to a residual queue
 //                 (warp-aggregated atomics) and counted per superbin.
 //   K2 bin        counting sort of the residual by superbin: scan of the
-//                 counts, scatter, and a list of work items of at most
-//                 pts_per_cta points (the GPU form of sorting points so many
-//                 share one polygon call, Sec. III-A / III).
-//   K3 cross      persistent CTAs take work items from an atomic counter;
-//                 each stages its superbin's record (candidates + clipped
-//                 edges) into shared memory with one cp.async.bulk copy
-//                 completed on an mbarrier (double-buffered: the next item's
-//                 copy flies while the current one is tested) and runs the
-//                 exact crossing-number test (Sec. III-A). Points whose leaf
-//                 holds a long edge list are tested by the whole warp: lanes
-//                 take strided edges and a ballot + popc gives the parity.
+//                 counts and a scatter, so points that share polygons sit
+//                 together (the GPU form of sorting the points so many share
+//                 one polygon call, Sec. III-A / III).
+//   K3 cross      persistent CTAs take chunks of pts_per_cta binned points
+//                 from an atomic counter. A chunk covers a contiguous range
+//                 of superbins whose records (candidates + clipped edges) are
+//                 contiguous in HBM; when they fit, one cp.async.bulk copy
+//                 completed on an mbarrier stages them in shared memory
+//                 (double-buffered: the next chunk's copy flies while the
+//                 current one is tested). The exact crossing-number test
+//                 (Sec. III-A) then runs per point; points whose leaf holds a
+//                 long edge list are tested by the whole warp: lanes take
+//                 strided edges and a ballot + popc gives the parity.
 #pragma once
 
 #include "pip_internal.cuh"
@@ -227,18 +229,28 @@ __device__ __forceinline__ uint32_t leaf_edges(const BlobView& b, uint32_t local
   return estart[b.words[local + 1]] - estart[b.words[local]];
 }
 
-// Test the residual points [first, first + count) of one work item whose
-// superbin record is `b`; writes the ids through `store`.
+// Test the residual points [first, first + count) of one work item. Each
+// point's superbin record lives either in the staged copy of the chunk's
+// contiguous record range (staged != nullptr, starting at 16-byte unit
+// region16 of the blobs) or in global memory. Ids go through `store`.
 template <class Store>
-__device__ __forceinline__ void test_item(const BlobView& b, const Residual* __restrict__ binned,
-                                          uint32_t first, uint32_t count, Store store) {
+__device__ __forceinline__ void test_chunk(const IndexView& ix, const Residual* __restrict__ binned,
+                                           uint32_t first, uint32_t count, const uint4* staged,
+                                           uint32_t region16, Store store) {
   const int lane = threadIdx.x & 31;
   const uint32_t warp_base = (threadIdx.x & ~31u);
   for (uint32_t base = warp_base; base < count; base += blockDim.x) {
     const uint32_t t = base + lane;
     const bool active = t < count;
     Residual r = make_uint4(0, 0, 0, 0);
-    if (active) r = binned[first + t];
+    const uint4* bp = ix.blobs;
+    if (active) {
+      r = binned[first + t];
+      const uint2 sd = ix.sbdesc[r.w >> SB_LOG2];
+      bp = staged ? staged + (sd.x - region16) : ix.blobs + sd.x;
+    }
+    BlobView b{nullptr, nullptr};
+    if (active) b = blob_view(bp);
     const uint32_t local = r.w & (SB_SLOTS - 1);
     const bool is_long = active && leaf_edges(b, local) > (uint32_t)LONG_LIST;
     int32_t id = -1;
@@ -250,7 +262,9 @@ __device__ __forceinline__ void test_item(const BlobView& b, const Residual* __r
       const int32_t px = (int32_t)__shfl_sync(0xffffffffu, r.x, j);
       const int32_t py = (int32_t)__shfl_sync(0xffffffffu, r.y, j);
       const uint32_t lj = __shfl_sync(0xffffffffu, local, j);
-      const int32_t v = test_point_warp(b, lj, px, py);
+      const unsigned long long pj =
+          __shfl_sync(0xffffffffu, (unsigned long long)(uintptr_t)bp, j);
+      const int32_t v = test_point_warp(blob_view((const uint4*)(uintptr_t)pj), lj, px, py);
       if (lane == j) id = v;
     }
     if (active) store(r, id);

@@ -58,16 +58,7 @@ __global__ void __launch_bounds__(K1_THREADS) k_classify_points(
 }
 
 // ------------------------------------------------------------------- K2
-// packed[sb] = points << 32 | work items (ceil(points / ppc)).
-__global__ void k_pack(const uint32_t* __restrict__ hist, int64_t n_sb, uint32_t ppc,
-                       uint64_t* __restrict__ packed) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_sb;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t c = hist[i];
-    packed[i] = ((uint64_t)c << 32) | (uint64_t)((c + ppc - 1) / ppc);
-  }
-}
-
+// Counting sort by superbin: off = exclusive scan of hist (in points).
 __global__ void k_scatter(const Residual* __restrict__ queue, const uint32_t* __restrict__ qcount,
                           const uint64_t* __restrict__ off, uint32_t* __restrict__ cursor,
                           Residual* __restrict__ binned) {
@@ -75,22 +66,8 @@ __global__ void k_scatter(const Residual* __restrict__ queue, const uint32_t* __
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const Residual e = queue[i];
     const uint32_t sb = e.w >> SB_LOG2;
-    const uint32_t pos = (uint32_t)(off[sb] >> 32) + atomicAdd(cursor + sb, 1u);
+    const uint32_t pos = (uint32_t)off[sb] + atomicAdd(cursor + sb, 1u);
     binned[pos] = e;
-  }
-}
-
-// items[w] = (superbin, first point, count, 0)
-__global__ void k_items(const uint32_t* __restrict__ hist, const uint64_t* __restrict__ off,
-                        int64_t n_sb, uint32_t ppc, uint4* __restrict__ items) {
-  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n_sb;
-       s += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t c = hist[s];
-    if (!c) continue;
-    const uint32_t first = (uint32_t)(off[s] >> 32);
-    const uint32_t w0 = (uint32_t)(off[s] & 0xFFFFFFFFu);
-    for (uint32_t t = 0, w = w0; t < c; t += ppc, ++w)
-      items[w] = make_uint4((uint32_t)s, first + t, min(ppc, c - t), 0u);
   }
 }
 
@@ -102,8 +79,7 @@ struct PlainStore {
 
 template <int STAGES>
 __global__ void __launch_bounds__(K3_THREADS) k_cross(IndexView ix, const Residual* __restrict__ binned,
-                                                      const uint4* __restrict__ items,
-                                                      const uint64_t* __restrict__ total_packed,
+                                                      const uint32_t* __restrict__ qcount, uint32_t ppc,
                                                       uint32_t* __restrict__ item_ctr,
                                                       int32_t* __restrict__ out,
                                                       uint32_t* __restrict__ status,
@@ -112,8 +88,10 @@ __global__ void __launch_bounds__(K3_THREADS) k_cross(IndexView ix, const Residu
   __shared__ __align__(8) uint64_t bar[STAGES];
   __shared__ uint32_t s_item[STAGES];
   __shared__ uint32_t s_staged[STAGES];
+  __shared__ uint32_t s_region[STAGES];
   __shared__ uint32_t s_abort;
-  const uint32_t n_items = (uint32_t)(*total_packed & 0xFFFFFFFFu);
+  const uint32_t n_res = *qcount;
+  const uint32_t n_items = (n_res + ppc - 1) / ppc;
   const uint32_t stage16 = stage_bytes >> 4;
   if (threadIdx.x == 0) {
     for (int i = 0; i < STAGES; ++i) mbar_init(&bar[i], 1);
@@ -125,18 +103,23 @@ __global__ void __launch_bounds__(K3_THREADS) k_cross(IndexView ix, const Residu
 #pragma unroll
   for (int i = 0; i < STAGES; ++i) phase[i] = 0;
 
-  // thread 0: claim the next item into stage st and start its copy
+  // thread 0: claim the next chunk into stage st and start its copy when the
+  // chunk's superbin records fit the stage
   auto claim = [&](int st) {
     const uint32_t w = atomicAdd(item_ctr, 1u);
     s_item[st] = w;
     s_staged[st] = 0;
     if (w < n_items) {
-      const uint4 it = items[w];
-      const uint2 sd = ix.sbdesc[it.x];
-      if (sd.y <= stage16) {
+      const uint32_t first = w * ppc;
+      const uint32_t last = min(first + ppc, n_res) - 1;
+      const uint2 da = ix.sbdesc[binned[first].w >> SB_LOG2];
+      const uint2 db = ix.sbdesc[binned[last].w >> SB_LOG2];
+      const uint32_t len16 = db.x + db.y - da.x;
+      if (len16 <= stage16) {
         fence_proxy_async();
-        bulk_load(stage_mem + (size_t)st * stage16, ix.blobs + sd.x, sd.y * 16u, &bar[st]);
+        bulk_load(stage_mem + (size_t)st * stage16, ix.blobs + da.x, len16 * 16u, &bar[st]);
         s_staged[st] = 1;
+        s_region[st] = da.x;
       }
     }
   };
@@ -148,23 +131,18 @@ __global__ void __launch_bounds__(K3_THREADS) k_cross(IndexView ix, const Residu
     const uint32_t w = s_item[cur];
     if (w >= n_items || s_abort) break;
     if (STAGES == 2 && threadIdx.x == 0) claim(cur ^ 1);
-    const uint4 it = items[w];
-    const uint2 sd = ix.sbdesc[it.x];
-    const void* base;
+    const uint32_t first = w * ppc;
+    const uint32_t count = min(ppc, n_res - first);
+    const uint4* staged = nullptr;
     if (s_staged[cur]) {
       if (!mbar_wait(&bar[cur], phase[cur])) {
         atomicOr(status, 1u);
         s_abort = 1;
       }
       phase[cur] ^= 1u;
-      base = stage_mem + (size_t)cur * stage16;
-    } else {
-      base = ix.blobs + sd.x;
+      staged = stage_mem + (size_t)cur * stage16;
     }
-    if (!s_abort) {
-      const BlobView b = blob_view(base);
-      test_item(b, binned, it.y, it.z, PlainStore{out});
-    }
+    if (!s_abort) test_chunk(ix, binned, first, count, staged, s_region[cur], PlainStore{out});
     __syncthreads();
     if (STAGES == 2) {
       cur ^= 1;
@@ -201,7 +179,7 @@ static int k3_smem_config(int stages, uint32_t& stage_bytes) {
 }
 
 static pip_status k3_launch(const IndexView& ix, int stages, const Residual* binned,
-                            const uint4* items, const uint64_t* total_packed, uint32_t* item_ctr,
+                            const uint32_t* qcount, uint32_t ppc, uint32_t* item_ctr,
                             int32_t* out, uint32_t* status, cudaStream_t s) {
   uint32_t stage_bytes = 0;
   const int smem = k3_smem_config(stages, stage_bytes);
@@ -216,28 +194,27 @@ static pip_status k3_launch(const IndexView& ix, int stages, const Residual* bin
   const int ctas_per_sm = std::max(1, (int)((200 * 1024) / (smem + 2048)));
   const unsigned grid = (unsigned)(num_sms() * std::min(ctas_per_sm, 4));
   if (stages == 2)
-    k_cross<2><<<grid, K3_THREADS, smem, s>>>(ix, binned, items, total_packed, item_ctr, out, status,
+    k_cross<2><<<grid, K3_THREADS, smem, s>>>(ix, binned, qcount, ppc, item_ctr, out, status,
                                               stage_bytes);
   else
-    k_cross<1><<<grid, K3_THREADS, smem, s>>>(ix, binned, items, total_packed, item_ctr, out, status,
+    k_cross<1><<<grid, K3_THREADS, smem, s>>>(ix, binned, qcount, ppc, item_ctr, out, status,
                                               stage_bytes);
   PIP_CUDA(cudaGetLastError());
   return PIP_OK;
 }
 
-pip_status k3_launch_public(const IndexView& ix, int stages, const Residual* binned, const uint4* items,
-                            const uint64_t* total_packed, uint32_t* item_ctr, int32_t* out,
+pip_status k3_launch_public(const IndexView& ix, int stages, const Residual* binned,
+                            const uint32_t* qcount, uint32_t ppc, uint32_t* item_ctr, int32_t* out,
                             uint32_t* status, cudaStream_t s) {
-  return k3_launch(ix, stages, binned, items, total_packed, item_ctr, out, status, s);
+  return k3_launch(ix, stages, binned, qcount, ppc, item_ctr, out, status, s);
 }
 
 // Scratch of one device-resident projection of n points.
 struct ProjScratch {
   DBuf<Residual> queue, binned;
   DBuf<uint32_t> hist;   // [n_sb] counts then [n_sb] cursors
-  DBuf<uint64_t> packed; // [n_sb] packed counts then [n_sb] offsets then [1] total
-  DBuf<uint4> items;
-  DBuf<uint32_t> ctr;    // [0] queue count, [1] item counter
+  DBuf<uint64_t> off;    // [n_sb] exclusive scan of the counts
+  DBuf<uint32_t> ctr;    // [0] queue count, [1] chunk counter
 };
 
 pip_status project_device(pip_set_s* S, const double* lon, const double* lat, int64_t n, int32_t* out,
@@ -249,16 +226,12 @@ pip_status project_device(pip_set_s* S, const double* lon, const double* lat, in
   const IndexView& ix = S->view;
   const int64_t n_sb = std::max<int64_t>(1, ix.n_sb);
   const uint32_t ppc = (uint32_t)std::max(1, S->opts.pts_per_cta);
-  const int64_t max_items = std::min<int64_t>(n, n_sb) + n / ppc + 1;
   ProjScratch w;
   if (!w.queue.alloc(al, n, s) || !w.binned.alloc(al, n, s) || !w.hist.alloc(al, 2 * n_sb, s) ||
-      !w.packed.alloc(al, 2 * n_sb + 1, s) || !w.items.alloc(al, max_items, s) || !w.ctr.alloc(al, 4, s))
+      !w.off.alloc(al, n_sb, s) || !w.ctr.alloc(al, 4, s))
     return fail(PIP_ENOMEM, "pip_project: scratch allocation failed");
   uint32_t* hist = w.hist.p;
   uint32_t* cursor = w.hist.p + n_sb;
-  uint64_t* packed = w.packed.p;
-  uint64_t* off = w.packed.p + n_sb;
-  uint64_t* total = w.packed.p + 2 * n_sb;
   int prof = -1;
   if (S->prof_cap > 0 && S->prof_n < S->prof_cap) {
     prof = S->prof_n++;
@@ -276,29 +249,22 @@ pip_status project_device(pip_set_s* S, const double* lon, const double* lat, in
     k_classify_points<false><<<g1, K1_THREADS, 0, s>>>(ix, lon, lat, n, out, w.queue.p, w.ctr.p, hist);
   PIP_CUDA(cudaGetLastError());
   if (prof >= 0) PIP_CUDA(cudaEventRecord(S->prof_ev[4 * prof + 1], s));
-  const unsigned gs = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_sb + 255) / 256, num_sms() * 8));
-  k_pack<<<gs, 256, 0, s>>>(hist, n_sb, ppc, packed);
-  PIP_CUDA(cudaGetLastError());
-  pip_status st = scan_u64(*al, packed, off, n_sb, total, s);
+  pip_status st = scan_u32_to_u64(*al, hist, w.off.p, n_sb, nullptr, s);
   if (st != PIP_OK) return st;
-  k_scatter<<<(unsigned)(num_sms() * 8), 256, 0, s>>>(w.queue.p, w.ctr.p, off, cursor, w.binned.p);
-  PIP_CUDA(cudaGetLastError());
-  k_items<<<gs, 256, 0, s>>>(hist, off, n_sb, ppc, w.items.p);
+  k_scatter<<<(unsigned)(num_sms() * 8), 256, 0, s>>>(w.queue.p, w.ctr.p, w.off.p, cursor, w.binned.p);
   PIP_CUDA(cudaGetLastError());
   if (prof >= 0) PIP_CUDA(cudaEventRecord(S->prof_ev[4 * prof + 2], s));
-  st = k3_launch(ix, S->opts.stage_depth, w.binned.p, w.items.p, total, w.ctr.p + 1, out, S->status.p, s);
+  st = k3_launch(ix, S->opts.stage_depth, w.binned.p, w.ctr.p, ppc, w.ctr.p + 1, out, S->status.p, s);
   if (st != PIP_OK) return st;
   if (prof >= 0) PIP_CUDA(cudaEventRecord(S->prof_ev[4 * prof + 3], s));
-  count_launches(5);  // K1, pack, scatter, items, K3 (scans count their own)
+  count_launches(3);  // K1, scatter, K3 (the scan counts its own)
   if (stats) {
     uint32_t c[2];
-    uint64_t t = 0;
     PIP_CUDA(cudaMemcpyAsync(c, w.ctr.p, sizeof(c), cudaMemcpyDeviceToHost, s));
-    PIP_CUDA(cudaMemcpyAsync(&t, total, sizeof(t), cudaMemcpyDeviceToHost, s));
     PIP_CUDA(cudaStreamSynchronize(s));
     stats->n = n;
     stats->residual = c[0];
-    stats->items = (int64_t)(t & 0xFFFFFFFFu);
+    stats->items = (c[0] + ppc - 1) / ppc;
   }
   return PIP_OK;
 }

@@ -81,9 +81,9 @@ def test_holes_and_islands(pipm, tiny_set_holes):
 
 
 OPTION_CASES = [
-    dict(max_depth=0),                                   # uniform grid
-    dict(max_depth=0, cell_log2=14),                     # fine uniform grid
-    dict(max_depth=0, cell_log2=22),                     # one coarse cell
+    dict(max_depth=-1),                                  # uniform grid
+    dict(max_depth=-1, cell_log2=14),                    # fine uniform grid
+    dict(max_depth=-1, cell_log2=22),                    # one coarse cell
     dict(fanout_log2=1, leaf_edges=2, size_ratio=64),    # deep quadtree
     dict(fanout_log2=3, leaf_edges=4),                   # fanout 64
     dict(stage_depth=1, pts_per_cta=7),                  # single stage, tiny items
