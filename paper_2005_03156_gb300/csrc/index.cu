@@ -281,6 +281,35 @@ __device__ __forceinline__ void cell_rect(const Grid& g, int shift, uint32_t cx,
   y1 = y0 + (1ll << shift);
 }
 
+// Does the segment a-b meet the closed rectangle [x0, x1m] x [y0, y1m]?
+// Separating-axis test: the box axes (coordinate overlap) and the segment's
+// normal (all four corners strictly on one side), in exact 128-bit integers.
+__device__ __forceinline__ bool seg_meets_rect(long long ax, long long ay, long long bx, long long by,
+                                               long long x0, long long y0, long long x1m,
+                                               long long y1m) {
+  if (max(ax, bx) < x0 || min(ax, bx) > x1m || max(ay, by) < y0 || min(ay, by) > y1m) return false;
+  const __int128 dx = bx - ax, dy = by - ay;
+  int pos = 0, neg = 0;
+  const long long cx[4] = {x0, x1m, x0, x1m}, cy[4] = {y0, y0, y1m, y1m};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __int128 v = dx * (__int128)(cy[i] - ay) - dy * (__int128)(cx[i] - ax);
+    pos += v > 0;
+    neg += v < 0;
+  }
+  return !(pos == 4 || neg == 4);
+}
+
+// Crossing rule of one normalised edge (ay < by) for the point (px, py).
+__device__ __forceinline__ uint32_t crosses_ll(int4 e, long long px, long long py) {
+  if (py < e.y || py >= e.w) return 0;
+  if (px >= (long long)max(e.x, e.z)) return 0;
+  if (px < (long long)min(e.x, e.z)) return 1;
+  const __int128 l = (__int128)(e.z - e.x) * (__int128)(py - e.y);
+  const __int128 r = (__int128)(e.w - e.y) * (__int128)(px - e.x);
+  return l > r ? 1u : 0u;
+}
+
 // 0 drop, 1 fold, 2 keep; the edge is normalised so that ay < by.
 __device__ __forceinline__ int clip_edge(int ax, int ay, int bx, int by, long long x0, long long y0,
                                          long long x1, long long y1, int4& out) {
@@ -297,7 +326,12 @@ __device__ __forceinline__ int clip_edge(int ax, int ay, int bx, int by, long lo
 }
 
 // Count (emit == nullptr) or emit the kept edges of each frontier candidate,
-// and compute its base parity.
+// and compute its base parity. When no edge of the candidate meets the
+// cell's closed lattice rectangle, its parity is the same at every lattice
+// point of the cell: two lattice segments that do not meet are at least
+// 1/(sqrt(2) W) apart, more than the infinitesimal shift that settles ties,
+// so no edge separates two points of the cell. The candidate then keeps no
+// edge and its base becomes that constant, taken at the lower-left point.
 template <bool FROM_POLY>
 __global__ void k_clip(Grid g, int shift, int64_t n_cand, const uint32_t* __restrict__ cd_cell,
                        const uint32_t* __restrict__ fc_x, const uint32_t* __restrict__ fc_y,
@@ -313,38 +347,53 @@ __global__ void k_clip(Grid g, int shift, int64_t n_cand, const uint32_t* __rest
     long long x0, y0, x1, y1;
     const uint32_t cell = cd_cell[c];
     cell_rect(g, shift, fc_x[cell], fc_y[cell], x0, y0, x1, y1);
-    uint32_t kept = 0, fold = 0;
+    uint32_t kept = 0, fold = 0, at_corner = 0;
+    bool touch = false;
     uint64_t w = emit ? emit_off[c] : 0;
     int4 e;
+    auto visit = [&](int ax, int ay, int bx, int by) {
+      const bool meets = seg_meets_rect(ax, ay, bx, by, x0, y0, x1 - 1, y1 - 1);
+      touch |= meets;
+      int k;
+      if (ay == by) {
+        // a horizontal edge never counts, but one that crosses the cell
+        // separates inside from outside: keep it so sub-cells see it
+        k = meets ? 2 : 0;
+        e = make_int4(ax, ay, bx, by);
+      } else {
+        k = clip_edge(ax, ay, bx, by, x0, y0, x1, y1, e);
+      }
+      fold ^= (k == 1);
+      if (k == 2) {
+        if (emit) emit[w++] = e;
+        at_corner ^= crosses_ll(e, x0, y0);
+        ++kept;
+      }
+    };
     if (FROM_POLY) {
       const int32_t p = cd_poly[c];
       for (int64_t r = pro[p]; r < pro[p + 1]; ++r) {
         const int64_t a = ring_off[r], b = ring_off[r + 1];
         for (int64_t i = a; i < b; ++i) {
           const int64_t j = (i + 1 == b) ? a : i + 1;
-          const int k = clip_edge(vx[i], vy[i], vx[j], vy[j], x0, y0, x1, y1, e);
-          fold ^= (k == 1);
-          if (k == 2) {
-            if (emit) emit[w++] = e;
-            ++kept;
-          }
+          visit(vx[i], vy[i], vx[j], vy[j]);
         }
       }
     } else {
       const uint64_t a = cd_src[c], b = a + cd_srcn[c];
       for (uint64_t i = a; i < b; ++i) {
         const int4 s = src_edges[i];
-        const int k = clip_edge(s.x, s.y, s.z, s.w, x0, y0, x1, y1, e);
-        fold ^= (k == 1);
-        if (k == 2) {
-          if (emit) emit[w++] = e;
-          ++kept;
-        }
+        visit(s.x, s.y, s.z, s.w);
       }
     }
     if (!emit) {
-      cd_kept[c] = kept;
-      cd_base[c] ^= (uint8_t)fold;
+      if (!touch) {
+        cd_kept[c] = 0;
+        cd_base[c] ^= (uint8_t)(fold ^ at_corner);
+      } else {
+        cd_kept[c] = kept;
+        cd_base[c] ^= (uint8_t)fold;
+      }
     }
   }
 }

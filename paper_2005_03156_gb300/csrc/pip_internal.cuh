@@ -14,7 +14,9 @@
 //            u32 cand[nc]           polygon id | base_parity << 31
 //            u32 edge_start[nc + 1] edge range of each candidate
 //            (pad to 16 bytes)
-//            int4 edge[ne]          (ax, ay, bx, by) with ay < by
+//            int4 edge[ne]          (ax, ay, bx, by) with ay <= by; an edge
+//                                   with ay == by is horizontal and never
+//                                   counts (kept only to mark the boundary)
 //   sbdesc uint2 per superbin: blob offset and size in 16-byte units.
 #pragma once
 
@@ -128,8 +130,8 @@ __device__ __forceinline__ bool quantize_double(double v, int32_t& q) {
 
 // ---------------------------------------------------------------------------
 // Crossing-number contribution (Sec. III-A) of a stored edge for the lattice
-// point (px, py). Stored edges have ay < by (horizontal edges never count and
-// are not stored; the even-odd parity does not depend on edge direction).
+// point (px, py). Stored edges have ay <= by (the even-odd parity does not
+// depend on edge direction); horizontal ones (ay == by) never count.
 // The edge counts iff ay <= py < by and its crossing with y = py lies
 // strictly right of px: wholly right counts, wholly at-or-left does not, and
 // otherwise the sign of (bx-ax)(py-ay) - (by-ay)(px-ax) decides (> 0 counts).

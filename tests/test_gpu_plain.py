@@ -231,3 +231,37 @@ def test_state_scale_sampled(pipm):
     idx = np.random.default_rng(44).choice(len(lon), 200_000, replace=False)
     want = oracle.join_hier(ps, lon[idx], lat[idx])
     assert (got[idx] == want).all(), int((got[idx] != want).sum())
+
+
+def kd_rectangles(rng, box, n):
+    """Axis-aligned partition of box by random kd splits (T-junctions,
+    many horizontal edges)."""
+    rects = [box]
+    while len(rects) < n:
+        i = int(np.argmax([(r[2] - r[0]) * (r[3] - r[1]) for r in rects]))
+        x0, y0, x1, y1 = rects.pop(i)
+        if (x1 - x0 >= y1 - y0 and x1 - x0 > 2) or y1 - y0 <= 2:
+            m = int(rng.integers(x0 + 1, x1))
+            rects += [(x0, y0, m, y1), (m, y0, x1, y1)]
+        else:
+            m = int(rng.integers(y0 + 1, y1))
+            rects += [(x0, y0, x1, m), (x0, m, x1, y1)]
+    return [[[(a, b), (c, b), (c, d), (a, d)]] for a, b, c, d in rects]
+
+
+@pytest.mark.parametrize("opts", [None, dict(leaf_edges=1, size_ratio=64), dict(max_depth=-1),
+                                  dict(cell_log2=8, fanout_log2=1)])
+def test_axis_aligned_partition(pipm, opts):
+    rng = np.random.default_rng(50)
+    box = (1000, 2000, 1000 + 40_000, 2000 + 30_000)
+    ps = pins.poly_set(kd_rectangles(rng, box, 400))
+    s = pipm.pip_set_load_i32(ps.vx, ps.vy, ps.ring_off, ps.poly_ring_off, opts=opts)
+    # every vertex, points one unit around vertices, and uniform lattice points
+    qx = np.concatenate([ps.vx, ps.vx + 1, ps.vx - 1, ps.vx, rng.integers(box[0] - 5, box[2] + 5, 100_000)])
+    qy = np.concatenate([ps.vy, ps.vy, ps.vy + 1, ps.vy - 1, rng.integers(box[1] - 5, box[3] + 5, 100_000)])
+    lon, lat = lattice_to_degrees(qx), lattice_to_degrees(qy)
+    got = project(pipm, s, lon, lat)
+    want = oracle.join_hier(ps, lon, lat)
+    assert (got == want).all(), int((got != want).sum())
+    inside = (qx >= box[0]) & (qx < box[2]) & (qy >= box[1]) & (qy < box[3])
+    assert (got[inside] >= 0).all() and (got[~inside] == -1).all()
