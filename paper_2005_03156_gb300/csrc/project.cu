@@ -100,8 +100,12 @@ __global__ void __launch_bounds__(K3_THREADS) k_cross(IndexView ix, const Residu
   }
   __syncthreads();
   uint32_t phase[STAGES];
+  bool pending[STAGES];  // thread 0: a copy into this stage is in flight
 #pragma unroll
-  for (int i = 0; i < STAGES; ++i) phase[i] = 0;
+  for (int i = 0; i < STAGES; ++i) {
+    phase[i] = 0;
+    pending[i] = false;
+  }
 
   // thread 0: claim the next chunk into stage st and start its copy when the
   // chunk's superbin records fit the stage
@@ -120,6 +124,7 @@ __global__ void __launch_bounds__(K3_THREADS) k_cross(IndexView ix, const Residu
         bulk_load(stage_mem + (size_t)st * stage16, ix.blobs + da.x, len16 * 16u, &bar[st]);
         s_staged[st] = 1;
         s_region[st] = da.x;
+        pending[st] = true;
       }
     }
   };
@@ -135,11 +140,13 @@ __global__ void __launch_bounds__(K3_THREADS) k_cross(IndexView ix, const Residu
     const uint32_t count = min(ppc, n_res - first);
     const uint4* staged = nullptr;
     if (s_staged[cur]) {
-      if (!mbar_wait(&bar[cur], phase[cur])) {
+      if (mbar_wait(&bar[cur], phase[cur])) {
+        phase[cur] ^= 1u;
+        pending[cur] = false;
+      } else {
         atomicOr(status, 1u);
         s_abort = 1;
       }
-      phase[cur] ^= 1u;
       staged = stage_mem + (size_t)cur * stage16;
     }
     if (!s_abort) test_chunk(ix, binned, first, count, staged, s_region[cur], PlainStore{out});
@@ -151,10 +158,11 @@ __global__ void __launch_bounds__(K3_THREADS) k_cross(IndexView ix, const Residu
       __syncthreads();
     }
   }
-  // never leave with a copy in flight: wait (bounded) for a claimed stage
+  // never leave with a copy in flight: wait (bounded) for any issued copy
+  // that no iteration consumed
   if (threadIdx.x == 0) {
     for (int st = 0; st < STAGES; ++st)
-      if (s_item[st] < n_items && s_staged[st] && st != cur) mbar_wait(&bar[st], phase[st]);
+      if (pending[st]) mbar_wait(&bar[st], phase[st]);
   }
 }
 
