@@ -84,7 +84,8 @@ typedef struct {
   int32_t size_ratio;   /* split while cell side * ratio > smallest candidate box side
                            (0 = auto, negative = off) */
   int32_t pts_per_cta;  /* residual points per crossing work item (0 = auto) */
-  int32_t stage_depth;  /* shared-memory stages in the crossing kernel, 1 or 2 (0 = auto) */
+  int32_t stage_depth;  /* shared-memory stages in the crossing kernel: 1 or 2, or
+                           negative for none (records read through L1/L2); 0 = auto */
   int32_t cand_mode;    /* 0 = auto, 1 = descend the box hierarchy, 2 = rasterize block boxes */
 } pip_build_opts;
 

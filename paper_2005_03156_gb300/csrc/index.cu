@@ -705,7 +705,8 @@ static void resolve_opts(const pip_build_opts& in, int64_t n_poly, long long w, 
   if (o.leaf_edges <= 0) o.leaf_edges = 16;
   if (o.size_ratio == 0) o.size_ratio = 16;
   if (o.pts_per_cta <= 0) o.pts_per_cta = 256;
-  if (o.stage_depth <= 0) o.stage_depth = 2;
+  if (o.stage_depth == 0) o.stage_depth = 2;
+  if (o.stage_depth < 0) o.stage_depth = -1;  // no shared-memory staging
   if (o.stage_depth > 2) o.stage_depth = 2;
   if (o.cand_mode <= 0) o.cand_mode = n_levels > 0 ? 1 : 2;
 }

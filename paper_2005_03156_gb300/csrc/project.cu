@@ -16,6 +16,9 @@ __global__ void __launch_bounds__(K1_THREADS) k_classify_points(
     IndexView ix, const double* __restrict__ lon, const double* __restrict__ lat, int64_t n,
     int32_t* __restrict__ out, Residual* __restrict__ queue, uint32_t* __restrict__ qcount,
     uint32_t* __restrict__ hist) {
+  __shared__ ResBuf rb;
+  if (threadIdx.x == 0) rb.count = 0;
+  __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t groups = (n + 3) / 4;
@@ -53,8 +56,10 @@ __global__ void __launch_bounds__(K1_THREADS) k_classify_points(
       for (int j = 0; j < 4; ++j)
         if (have[j]) out[i0 + j] = id[j];
     }
-    append_residual(mask, qx, qy, d, (uint32_t)i0, queue, qcount, hist, 0u);
+    append_residual(rb, mask, qx, qy, d, (uint32_t)i0, hist, 0u);
+    flush_residual(rb, false, queue, qcount);
   }
+  flush_residual(rb, true, queue, qcount);
 }
 
 // ------------------------------------------------------------------- K2
@@ -166,6 +171,27 @@ __global__ void __launch_bounds__(K3_THREADS) k_cross(IndexView ix, const Residu
   }
 }
 
+// K3 without shared-memory staging: records are read through L1/L2. Best
+// when a chunk's points are spread over more superbins than fit a stage.
+__global__ void __launch_bounds__(K3_THREADS) k_cross_direct(IndexView ix,
+                                                             const Residual* __restrict__ binned,
+                                                             const uint32_t* __restrict__ qcount,
+                                                             uint32_t ppc, uint32_t* __restrict__ item_ctr,
+                                                             int32_t* __restrict__ out) {
+  __shared__ uint32_t s_w;
+  const uint32_t n_res = *qcount;
+  const uint32_t n_items = (n_res + ppc - 1) / ppc;
+  while (true) {
+    if (threadIdx.x == 0) s_w = atomicAdd(item_ctr, 1u);
+    __syncthreads();
+    const uint32_t w = s_w;
+    __syncthreads();
+    if (w >= n_items) break;
+    const uint32_t first = w * ppc;
+    test_chunk(ix, binned, first, min(ppc, n_res - first), nullptr, 0u, PlainStore{out});
+  }
+}
+
 // ------------------------------------------------------------------- host
 static void init_pool_once() {
   static std::once_flag f[64];
@@ -189,6 +215,12 @@ static int k3_smem_config(int stages, uint32_t& stage_bytes) {
 static pip_status k3_launch(const IndexView& ix, int stages, const Residual* binned,
                             const uint32_t* qcount, uint32_t ppc, uint32_t* item_ctr,
                             int32_t* out, uint32_t* status, cudaStream_t s) {
+  if (stages < 0) {
+    const unsigned grid = (unsigned)(num_sms() * 8);
+    k_cross_direct<<<grid, K3_THREADS, 0, s>>>(ix, binned, qcount, ppc, item_ctr, out);
+    PIP_CUDA(cudaGetLastError());
+    return PIP_OK;
+  }
   uint32_t stage_bytes = 0;
   const int smem = k3_smem_config(stages, stage_bytes);
   static bool attr_set[3] = {false, false, false};

@@ -88,6 +88,7 @@ OPTION_CASES = [
     dict(fanout_log2=3, leaf_edges=4),                   # fanout 64
     dict(stage_depth=1, pts_per_cta=7),                  # single stage, tiny items
     dict(stage_depth=2, pts_per_cta=1000),               # items larger than the CTA
+    dict(stage_depth=-1, pts_per_cta=300),               # no staging
     dict(cand_mode=2),                                   # box rasterization
     dict(cand_mode=1, size_ratio=-1, leaf_edges=1000),   # few splits, long lists (warp ballots)
 ]
