@@ -68,24 +68,13 @@ __device__ __forceinline__ void lookup4(const IndexView& ix, const int32_t (&qx)
   }
 }
 
-// Residual entries are gathered per CTA in shared memory and flushed to
-// the global queue in coalesced blocks, so the queue counter sees one atomic
-// per ~RES_CAP entries instead of one per warp step (same-address atomics
-// serialise in L2).
-constexpr int RES_CAP = 2048;
-
-struct ResBuf {
-  Residual e[RES_CAP];
-  uint32_t count;
-  uint32_t base;
-};
-
-// Append up to 4 residual points of this lane to the CTA buffer (one shared
-// atomic per warp) and count them per superbin (hist may be offset per set).
-__device__ __forceinline__ void append_residual(ResBuf& rb, uint32_t mask, const int32_t (&qx)[4],
+// Append up to 4 residual points of this lane to the queue with one atomic
+// per warp; count them per superbin (hist may be offset per set).
+__device__ __forceinline__ void append_residual(uint32_t mask, const int32_t (&qx)[4],
                                                 const int32_t (&qy)[4], const uint32_t (&d)[4],
-                                                uint32_t idx0, uint32_t* __restrict__ hist,
-                                                uint32_t slot_add) {
+                                                uint32_t idx0, Residual* __restrict__ queue,
+                                                uint32_t* __restrict__ qcount,
+                                                uint32_t* __restrict__ hist, uint32_t slot_add) {
   const uint32_t full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   if (!__any_sync(full, mask != 0u)) return;
@@ -97,33 +86,16 @@ __device__ __forceinline__ void append_residual(ResBuf& rb, uint32_t mask, const
     if (lane >= o) incl += t;
   }
   uint32_t base = 0;
-  if (lane == 31) base = atomicAdd(&rb.count, incl);
+  if (lane == 31) base = atomicAdd(qcount, incl);
   base = __shfl_sync(full, base, 31) + incl - r;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     if (mask & (1u << j)) {
       const uint32_t slot = (d[j] & PAYLOAD_MASK) + slot_add;
-      rb.e[base++] = make_uint4((uint32_t)qx[j], (uint32_t)qy[j], idx0 + j, slot);
+      queue[base++] = make_uint4((uint32_t)qx[j], (uint32_t)qy[j], idx0 + j, slot);
       atomicAdd(hist + (slot >> SB_LOG2), 1u);
     }
   }
-}
-
-// Whole CTA: when `force` or when another step could overflow the buffer,
-// move the buffered entries to the global queue. Ends with a barrier.
-__device__ __forceinline__ void flush_residual(ResBuf& rb, bool force, Residual* __restrict__ queue,
-                                               uint32_t* __restrict__ qcount) {
-  __syncthreads();
-  const uint32_t c = rb.count;
-  __syncthreads();  // every thread has read the count before anyone appends again
-  if (c == 0 || (!force && c + 4u * blockDim.x <= (uint32_t)RES_CAP)) return;
-  if (threadIdx.x == 0) rb.base = atomicAdd(qcount, c);
-  __syncthreads();
-  const uint32_t g = rb.base;
-  for (uint32_t i = threadIdx.x; i < c; i += blockDim.x) queue[g + i] = rb.e[i];
-  __syncthreads();
-  if (threadIdx.x == 0) rb.count = 0;
-  __syncthreads();
 }
 
 // Classify 4 points; returns their ids (-1 for residual ones) and the

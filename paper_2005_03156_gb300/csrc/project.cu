@@ -9,43 +9,55 @@
 namespace pip {
 
 // ------------------------------------------------------------------- K1
-// VEC: lon/lat are 16-byte aligned; each thread takes 4 consecutive points
-// per step (two double2 loads per coordinate, one int4 store).
+// Loads of one step: 4 consecutive points per thread.
+template <bool VEC>
+__device__ __forceinline__ void load4(const double* __restrict__ lon, const double* __restrict__ lat,
+                                      int64_t n, int64_t g, double (&x)[4], double (&y)[4]) {
+  const int64_t i0 = g * 4;
+  if (VEC && i0 + 3 < n) {
+    const double2 a0 = __ldcs(reinterpret_cast<const double2*>(lon) + 2 * g);
+    const double2 a1 = __ldcs(reinterpret_cast<const double2*>(lon) + 2 * g + 1);
+    const double2 b0 = __ldcs(reinterpret_cast<const double2*>(lat) + 2 * g);
+    const double2 b1 = __ldcs(reinterpret_cast<const double2*>(lat) + 2 * g + 1);
+    x[0] = a0.x; x[1] = a0.y; x[2] = a1.x; x[3] = a1.y;
+    y[0] = b0.x; y[1] = b0.y; y[2] = b1.x; y[3] = b1.y;
+  } else {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const bool have = i0 + j < n;
+      x[j] = have ? lon[i0 + j] : __longlong_as_double(0x7FF8000000000000ll);  // NaN: invalid
+      y[j] = have ? lat[i0 + j] : 0.0;
+    }
+  }
+}
+
+// VEC: lon/lat/out are 16-byte aligned; each thread takes 4 consecutive
+// points per step (two double2 loads per coordinate, one int4 store). The
+// grid is persistent (one wave) and the next step's loads are issued before
+// the current step's trie walk, so the stream's DRAM latency overlaps the
+// dependent lookups.
 template <bool VEC>
 __global__ void __launch_bounds__(K1_THREADS) k_classify_points(
     IndexView ix, const double* __restrict__ lon, const double* __restrict__ lat, int64_t n,
     int32_t* __restrict__ out, Residual* __restrict__ queue, uint32_t* __restrict__ qcount,
     uint32_t* __restrict__ hist) {
-  __shared__ ResBuf rb;
-  if (threadIdx.x == 0) rb.count = 0;
-  __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t groups = (n + 3) / 4;
   // iterate whole warps together so warp-level appends stay uniform
   const int64_t rounds = (groups + stride - 1) / stride;
+  double nx[4], ny[4];
+  load4<VEC>(lon, lat, n, tid, nx, ny);
   for (int64_t it = 0; it < rounds; ++it) {
     const int64_t g = it * stride + tid;
     const int64_t i0 = g * 4;
     double x[4], y[4];
-    bool have[4];
-    if (VEC && i0 + 3 < n) {
-      const double2 a0 = __ldcs(reinterpret_cast<const double2*>(lon) + 2 * g);
-      const double2 a1 = __ldcs(reinterpret_cast<const double2*>(lon) + 2 * g + 1);
-      const double2 b0 = __ldcs(reinterpret_cast<const double2*>(lat) + 2 * g);
-      const double2 b1 = __ldcs(reinterpret_cast<const double2*>(lat) + 2 * g + 1);
-      x[0] = a0.x; x[1] = a0.y; x[2] = a1.x; x[3] = a1.y;
-      y[0] = b0.x; y[1] = b0.y; y[2] = b1.x; y[3] = b1.y;
 #pragma unroll
-      for (int j = 0; j < 4; ++j) have[j] = true;
-    } else {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        have[j] = i0 + j < n;
-        x[j] = have[j] ? lon[i0 + j] : __longlong_as_double(0x7FF8000000000000ll);
-        y[j] = have[j] ? lat[i0 + j] : 0.0;
-      }
+    for (int j = 0; j < 4; ++j) {
+      x[j] = nx[j];
+      y[j] = ny[j];
     }
+    if (it + 1 < rounds) load4<VEC>(lon, lat, n, g + stride, nx, ny);
     int32_t id[4], qx[4], qy[4];
     uint32_t d[4];
     uint32_t mask = classify4(ix, x, y, id, qx, qy, d);
@@ -54,12 +66,10 @@ __global__ void __launch_bounds__(K1_THREADS) k_classify_points(
     } else {
 #pragma unroll
       for (int j = 0; j < 4; ++j)
-        if (have[j]) out[i0 + j] = id[j];
+        if (i0 + j < n) out[i0 + j] = id[j];
     }
-    append_residual(rb, mask, qx, qy, d, (uint32_t)i0, hist, 0u);
-    flush_residual(rb, false, queue, qcount);
+    append_residual(mask, qx, qy, d, (uint32_t)i0, queue, qcount, hist, 0u);
   }
-  flush_residual(rb, true, queue, qcount);
 }
 
 // ------------------------------------------------------------------- K2
@@ -216,7 +226,12 @@ static pip_status k3_launch(const IndexView& ix, int stages, const Residual* bin
                             const uint32_t* qcount, uint32_t ppc, uint32_t* item_ctr,
                             int32_t* out, uint32_t* status, cudaStream_t s) {
   if (stages < 0) {
-    const unsigned grid = (unsigned)(num_sms() * 8);
+    static int occ = 0;
+    if (!occ) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cross_direct, K3_THREADS, 0);
+      occ = std::max(1, occ);
+    }
+    const unsigned grid = (unsigned)(num_sms() * occ);
     k_cross_direct<<<grid, K3_THREADS, 0, s>>>(ix, binned, qcount, ppc, item_ctr, out);
     PIP_CUDA(cudaGetLastError());
     return PIP_OK;
@@ -281,8 +296,13 @@ pip_status project_device(pip_set_s* S, const double* lon, const double* lat, in
   PIP_CUDA(cudaMemsetAsync(w.ctr.p, 0, 4 * sizeof(uint32_t), s));
   const bool vec = ((uintptr_t)lon % 16 == 0) && ((uintptr_t)lat % 16 == 0) && ((uintptr_t)out % 16 == 0);
   const int64_t groups = (n + 3) / 4;
+  static int occ1 = 0;
+  if (!occ1) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_classify_points<true>, K1_THREADS, 0);
+    occ1 = std::max(1, occ1);
+  }
   const unsigned g1 = (unsigned)std::max<int64_t>(
-      1, std::min<int64_t>((groups + K1_THREADS - 1) / K1_THREADS, (int64_t)num_sms() * 8));
+      1, std::min<int64_t>((groups + K1_THREADS - 1) / K1_THREADS, (int64_t)num_sms() * occ1));
   if (vec)
     k_classify_points<true><<<g1, K1_THREADS, 0, s>>>(ix, lon, lat, n, out, w.queue.p, w.ctr.p, hist);
   else
