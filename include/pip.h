@@ -79,7 +79,8 @@ typedef struct {
   int32_t cell_log2;    /* log2 side of a top-level cell in lattice units (0 = auto) */
   int32_t max_depth;    /* subdivision levels below the top grid (0 = auto, < 0 = none:
                            a uniform grid) */
-  int32_t fanout_log2;  /* a split cell has 4^fanout_log2 children (0 = auto = 2) */
+  int32_t fanout_log2;  /* reported only: a split cell always has 4 x 4 children, held
+                           in one 32-byte trie node */
   int32_t leaf_edges;   /* split a boundary cell holding more kept edges than this (0 = auto) */
   int32_t size_ratio;   /* split while cell side * ratio > smallest candidate box side
                            (0 = auto, negative = off) */

@@ -407,8 +407,9 @@ __global__ void k_classify(int64_t n_cell, const uint64_t* __restrict__ fc_coff,
                            const int4* __restrict__ poly_box, const uint32_t* __restrict__ fc_slot,
                            uint32_t* __restrict__ desc, uint32_t* __restrict__ fc_nk,
                            uint32_t* __restrict__ fc_ne, uint32_t* __restrict__ fc_leaf,
-                           uint32_t* __restrict__ fc_split, int shift, int can_split,
-                           uint32_t leaf_edges, int size_ratio, unsigned long long* counters) {
+                           uint32_t* __restrict__ fc_split, int32_t* __restrict__ fc_val, int shift,
+                           int can_split, uint32_t leaf_edges, int size_ratio,
+                           unsigned long long* counters) {
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cell;
        c += (int64_t)gridDim.x * blockDim.x) {
     uint32_t nk = 0, ne = 0, first = 0xFFFFFFFFu;
@@ -437,15 +438,16 @@ __global__ void k_classify(int64_t n_cell, const uint64_t* __restrict__ fc_coff,
       }
     }
     uint32_t leaf = 0, split = 0;
-    if (nk == 0) {
-      desc[fc_slot[c]] = make_desc(TAG_EMPTY, 0);
+    int32_t val = 0;
+    if (nk == 0) {  // EMPTY
+      if (desc) desc[fc_slot[c]] = make_desc(TAG_EMPTY, 0);
       atomicAdd(counters + 0, 1ull);
-      nk = 0;
+      val = -1;
       ne = 0;
-    } else if (nk == 1 && first_full) {
-      desc[fc_slot[c]] = make_desc(TAG_INTERIOR, (uint32_t)cd_poly[first]);
+    } else if (nk == 1 && first_full) {  // INTERIOR (keeps its one full candidate)
+      if (desc) desc[fc_slot[c]] = make_desc(TAG_INTERIOR, (uint32_t)cd_poly[first]);
       atomicAdd(counters + 1, 1ull);
-      nk = 0;
+      val = cd_poly[first];
       ne = 0;
     } else {
       const long long side = 1ll << shift;
@@ -460,7 +462,76 @@ __global__ void k_classify(int64_t n_cell, const uint64_t* __restrict__ fc_coff,
     fc_ne[c] = ne;
     fc_leaf[c] = leaf;
     fc_split[c] = split;
+    fc_val[c] = val;
   }
+}
+
+// Children of one split cell (frontier cells p*16 .. p*16+15): give each
+// EMPTY / INTERIOR child a 2-bit code into the node's 4-entry palette. A
+// child whose value does not fit the palette becomes a leaf instead (its
+// one full candidate, or none, then answers through the crossing test).
+__global__ void k_palette(int64_t n_parent, uint32_t* __restrict__ fc_leaf,
+                          const uint32_t* __restrict__ fc_split, const int32_t* __restrict__ fc_val,
+                          TrieNode* __restrict__ nodes, unsigned long long* counters) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_parent;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t codes = 0;
+    int32_t pal[4] = {-1, -1, -1, -1};
+    int np = 0;
+    for (int sub = 0; sub < NODE_FAN; ++sub) {
+      const int64_t c = p * NODE_FAN + sub;
+      if (fc_leaf[c] || fc_split[c]) continue;
+      const int32_t v = fc_val[c];
+      int j = 0;
+      while (j < np && pal[j] != v) ++j;
+      if (j == np) {
+        if (np == 4) {
+          fc_leaf[c] = 1;
+          atomicAdd(counters + 2, 1ull);
+          continue;
+        }
+        pal[np++] = v;
+      }
+      codes |= (uint32_t)j << (2 * sub);
+    }
+    TrieNode& nd = nodes[p];
+    nd.codes = codes;
+    for (int j = 0; j < 4; ++j) nd.pal[j] = pal[j];
+  }
+}
+
+// Leaf / split masks and rank bases of each node (after the ranks exist).
+__global__ void k_node_finish(int64_t n_parent, const uint32_t* __restrict__ fc_leaf,
+                              const uint32_t* __restrict__ fc_split,
+                              const uint64_t* __restrict__ leaf_rank,
+                              const uint64_t* __restrict__ split_rank, uint32_t slot_base,
+                              uint64_t node_base, TrieNode* __restrict__ nodes) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_parent;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t lm = 0, cm = 0;
+    int64_t first_leaf = -1, first_split = -1;
+    for (int sub = 0; sub < NODE_FAN; ++sub) {
+      const int64_t c = p * NODE_FAN + sub;
+      if (fc_leaf[c]) {
+        lm |= 1u << sub;
+        if (first_leaf < 0) first_leaf = c;
+      } else if (fc_split[c]) {
+        cm |= 1u << sub;
+        if (first_split < 0) first_split = c;
+      }
+    }
+    TrieNode& nd = nodes[p];
+    nd.masks = lm | (cm << 16);
+    nd.leaf_base = first_leaf >= 0 ? slot_base + (uint32_t)leaf_rank[first_leaf] : 0u;
+    nd.child_base = first_split >= 0 ? (uint32_t)(node_base + split_rank[first_split]) : 0u;
+  }
+}
+
+__global__ void k_eff_nk(int64_t n, const uint32_t* __restrict__ fc_nk, const uint32_t* __restrict__ fc_leaf,
+                         const uint32_t* __restrict__ fc_split, uint32_t* __restrict__ out) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
+       c += (int64_t)gridDim.x * blockDim.x)
+    out[c] = (fc_leaf[c] | fc_split[c]) ? fc_nk[c] : 0u;
 }
 
 // Boundary cells: write LEAF / CHILD descriptors, record leaf -> cell, and
@@ -483,10 +554,10 @@ __global__ void k_boundary(int64_t n_cell, const uint64_t* __restrict__ fc_coff,
     if (!leaf && !split) continue;
     if (leaf) {
       const uint64_t r = leaf_rank[c];
-      desc[fc_slot[c]] = make_desc(TAG_LEAF, slot_base + (uint32_t)r);
+      if (desc) desc[fc_slot[c]] = make_desc(TAG_LEAF, slot_base + (uint32_t)r);
       leaf_cell[r] = (uint32_t)c;
-    } else {
-      desc[fc_slot[c]] = make_desc(TAG_CHILD, (uint32_t)(child_base + split_rank[c] * (uint64_t)fan));
+    } else if (desc) {
+      desc[fc_slot[c]] = make_desc(TAG_CHILD, (uint32_t)(child_base + split_rank[c]));
     }
     uint64_t w = kc_off[c];
     for (uint64_t i = fc_coff[c]; i < fc_coff[c + 1]; ++i) {
@@ -698,7 +769,7 @@ static void resolve_opts(const pip_build_opts& in, int64_t n_poly, long long w, 
     while (s < 30 && area / std::ldexp(1.0, 2 * s) > cells_cap) ++s;
     o.cell_log2 = std::max(4, std::min(30, s));
   }
-  if (o.fanout_log2 <= 0) o.fanout_log2 = 2;
+  o.fanout_log2 = NODE_K;  // trie nodes hold 4 x 4 children
   if (o.max_depth == 0) o.max_depth = std::max(0, std::min(8, (o.cell_log2 - 6) / o.fanout_log2));
   else if (o.max_depth < 0) o.max_depth = 0;  // uniform grid
   o.max_depth = std::min(o.max_depth, std::max(0, (o.cell_log2 - 1) / o.fanout_log2));
@@ -833,8 +904,8 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
   Grid g;
   pip_build_opts o;
   CHECK(build_grid(S, g, o, al, s));
-  const int k = o.fanout_log2;
-  const int fan = 1 << (2 * k);
+  const int k = NODE_K;
+  const int fan = NODE_FAN;
   HierBufs hb;
   Hier h;
   CHECK(build_hierarchy(S, al, s, hb, h, err));
@@ -849,10 +920,10 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
   uint64_t top_total = 0;
   CHECK(top_candidates(S, al, s, h, g, o.cand_mode, top_cnt, top_coff, top_ids, top_total));
 
-  unsigned long long* counters = nullptr;  // [0] empty, [1] interior
+  unsigned long long* counters = nullptr;  // [0] empty, [1] interior, [2] palette overflows
   DBuf<unsigned long long> cnt_buf;
-  ALLOC(cnt_buf, 2);
-  PIP_CUDA(cudaMemsetAsync(cnt_buf.p, 0, 3 * sizeof(unsigned long long), s));
+  ALLOC(cnt_buf, 3);
+  PIP_CUDA(cudaMemsetAsync(cnt_buf.p, 0, 4 * sizeof(unsigned long long), s));
   counters = cnt_buf.p;
 
   // per-level outputs
@@ -861,7 +932,10 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
   std::vector<DBuf<uint4>> blob_lv;
   std::vector<DBuf<uint2>> sbd_lv;
   std::vector<int64_t> blob_len, sb_len;
+  std::vector<DBuf<TrieNode>> node_lv;  // nodes of each level's split cells
+  std::vector<int64_t> node_len;
   int64_t table_total = top_cells;
+  int64_t node_total = 0;
   desc_lv.emplace_back();
   ALLOC(desc_lv[0], top_cells);
   PIP_CUDA(cudaMemsetAsync(desc_lv[0].p, 0, (top_cells + 1) * sizeof(uint32_t), s));
@@ -926,15 +1000,27 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
     }
     PIP_CUDA(cudaGetLastError());
     // classify
-    DBuf<uint32_t> fnk, fne, fleaf, fsplit;
+    DBuf<uint32_t> fnk, fne, fleaf, fsplit, fnk_eff;
+    DBuf<int32_t> fval;
     ALLOC(fnk, n_cell);
     ALLOC(fne, n_cell);
     ALLOC(fleaf, n_cell);
     ALLOC(fsplit, n_cell);
+    ALLOC(fval, n_cell);
+    ALLOC(fnk_eff, n_cell);
     k_classify<<<blocks_for(n_cell), TB, 0, s>>>(n_cell, fcoff.p, cd_poly.p, cd_kept.p, cd_base.p,
-                                                 cd_keep.p, S->poly_box.p, fslot.p, desc_lv[lv].p,
-                                                 fnk.p, fne.p, fleaf.p, fsplit.p, shift, can_split ? 1 : 0,
+                                                 cd_keep.p, S->poly_box.p, fslot.p,
+                                                 lv == 0 ? desc_lv[0].p : nullptr, fnk.p, fne.p, fleaf.p,
+                                                 fsplit.p, fval.p, shift, can_split ? 1 : 0,
                                                  (uint32_t)o.leaf_edges, o.size_ratio, counters);
+    PIP_CUDA(cudaGetLastError());
+    const int64_t n_parent = lv == 0 ? 0 : n_cell / fan;
+    if (lv > 0) {  // palettes of the parents' nodes (may turn children into leaves)
+      k_palette<<<blocks_for(n_parent), TB, 0, s>>>(n_parent, fleaf.p, fsplit.p, fval.p,
+                                                    node_lv.back().p, counters);
+      PIP_CUDA(cudaGetLastError());
+    }
+    k_eff_nk<<<blocks_for(n_cell), TB, 0, s>>>(n_cell, fnk.p, fleaf.p, fsplit.p, fnk_eff.p);
     PIP_CUDA(cudaGetLastError());
     // ranks
     DBuf<uint64_t> leaf_rank, split_rank, kc_off, tots;
@@ -942,17 +1028,23 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
     ALLOC(split_rank, n_cell + 1);
     ALLOC(kc_off, n_cell + 1);
     ALLOC(tots, 3);
-    PIP_CUDA(cudaMemsetAsync(fnk.p + n_cell, 0, sizeof(uint32_t), s));
+    PIP_CUDA(cudaMemsetAsync(fnk_eff.p + n_cell, 0, sizeof(uint32_t), s));
     CHECK(scan_u32_to_u64(*al, fleaf.p, leaf_rank.p, n_cell, tots.p + 0, s));
     CHECK(scan_u32_to_u64(*al, fsplit.p, split_rank.p, n_cell, tots.p + 1, s));
-    CHECK(scan_u32_to_u64(*al, fnk.p, kc_off.p, n_cell + 1, tots.p + 2, s));
+    CHECK(scan_u32_to_u64(*al, fnk_eff.p, kc_off.p, n_cell + 1, tots.p + 2, s));
     uint64_t t3[3];
     CHECK(d2h(t3, tots.p, 3, s));
     const int64_t n_leaf = (int64_t)t3[0], n_split = (int64_t)t3[1], n_kc = (int64_t)t3[2];
-    const uint64_t child_base = (uint64_t)table_total;
-    if (child_base + (uint64_t)n_split * fan >= (1ull << 30) ||
+    const uint64_t child_base = (uint64_t)(node_total + (lv > 0 ? node_len.back() : 0));
+    if (child_base + (uint64_t)n_split >= (1ull << 30) ||
         (uint64_t)slot_base + (uint64_t)n_leaf + SB_SLOTS >= (1ull << 30))
       return fail(PIP_ERANGE, "index build: index exceeds 2^30 entries; raise cell_log2");
+    if (lv > 0) {  // masks and bases of the parents' nodes
+      k_node_finish<<<blocks_for(n_parent), TB, 0, s>>>(n_parent, fleaf.p, fsplit.p, leaf_rank.p,
+                                                        split_rank.p, slot_base, child_base,
+                                                        node_lv.back().p);
+      PIP_CUDA(cudaGetLastError());
+    }
     // boundary cells: descriptors + kept candidate compaction
     DBuf<uint32_t> leaf_cell, kc_cnt, kc_srcn, kc_cell;
     DBuf<int32_t> kc_poly;
@@ -969,8 +1061,8 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
     k_boundary<<<blocks_for(n_cell), TB, 0, s>>>(
         n_cell, fcoff.p, cd_keep.p, cd_poly.p, cd_base.p, cd_kept.p, lv ? cd_src.p : nullptr,
         lv ? cd_srcn.p : nullptr, fslot.p, fleaf.p, fsplit.p, leaf_rank.p, split_rank.p, kc_off.p,
-        desc_lv[lv].p, slot_base, child_base, fan, leaf_cell.p, kc_poly.p, kc_base.p, kc_cnt.p,
-        kc_src.p, kc_srcn.p, kc_cell.p);
+        lv == 0 ? desc_lv[0].p : nullptr, slot_base, child_base, fan, leaf_cell.p, kc_poly.p,
+        kc_base.p, kc_cnt.p, kc_src.p, kc_srcn.p, kc_cell.p);
     PIP_CUDA(cudaGetLastError());
     // kept edges of every kept candidate
     uint64_t n_ke = 0;
@@ -1076,12 +1168,12 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
         kc_eoff.p, S->poly_box.p, nullptr, coff.p, nfx.p, nfy.p, nslot.p, ncell.p, npoly.p, nbase.p,
         nsrc.p, nsrcn.p);
     PIP_CUDA(cudaGetLastError());
-    // the child tables of this level's split cells
-    desc_lv.emplace_back();
-    ALLOC(desc_lv.back(), n_child);
-    PIP_CUDA(cudaMemsetAsync(desc_lv.back().p, 0, (n_child + 1) * sizeof(uint32_t), s));
-    desc_len.push_back(n_child);
-    table_total += n_child;
+    // the nodes of this level's split cells (filled while their children are classified)
+    node_total = (int64_t)child_base;
+    node_lv.emplace_back();
+    ALLOC(node_lv.back(), n_split);
+    PIP_CUDA(cudaMemsetAsync(node_lv.back().p, 0, (n_split + 1) * sizeof(TrieNode), s));
+    node_len.push_back(n_split);
     // advance
     fx = std::move(nfx);
     fy = std::move(nfy);
@@ -1098,19 +1190,24 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
     PIP_CUDA(cudaStreamSynchronize(s));
   }
 
-  // concatenate the table and the blobs
+  // concatenate the nodes and the blobs; the top grid is the table
   S->table.release();
+  S->nodes.release();
   S->blobs.release();
   S->sbdesc.release();
-  if (!S->table.alloc(al, (size_t)table_total, s)) return fail(PIP_ENOMEM, "index: table");
+  S->table = std::move(desc_lv[0]);
+  int64_t n_nodes = 0;
+  for (int64_t l : node_len) n_nodes += l;
+  if (!S->nodes.alloc(al, (size_t)(2 * n_nodes + 2), s)) return fail(PIP_ENOMEM, "index: nodes");
   {
     int64_t at = 0;
-    for (size_t i = 0; i < desc_lv.size(); ++i) {
-      PIP_CUDA(cudaMemcpyAsync(S->table.p + at, desc_lv[i].p, desc_len[i] * sizeof(uint32_t),
+    for (size_t i = 0; i < node_lv.size(); ++i) {
+      PIP_CUDA(cudaMemcpyAsync(S->nodes.p + 2 * at, node_lv[i].p, node_len[i] * sizeof(TrieNode),
                                cudaMemcpyDeviceToDevice, s));
-      at += desc_len[i];
+      at += node_len[i];
     }
   }
+  table_total = top_cells + 8 * n_nodes;
   // blobs padded by one 16-byte unit so bulk copies never read past the end
   if (!S->blobs.alloc(al, (size_t)blob_total16 + 1, s)) return fail(PIP_ENOMEM, "index: blobs");
   if (!S->sbdesc.alloc(al, (size_t)sb_total + 1, s)) return fail(PIP_ENOMEM, "index: sbdesc");
@@ -1127,8 +1224,8 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
   }
   uint32_t e2 = 0;
   CHECK(d2h(&e2, err.p, 1, s));
-  unsigned long long hc[2];
-  CHECK(d2h(hc, counters, 2, s));
+  unsigned long long hc[3];
+  CHECK(d2h(hc, counters, 3, s));
   PIP_CUDA(cudaEventRecord(ev1, s));
   PIP_CUDA(cudaEventSynchronize(ev1));
   float ms = 0;
@@ -1142,10 +1239,10 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
   v.nx = g.nx;
   v.ny = g.ny;
   v.s0 = g.s0;
-  v.k = k;
   v.depth = depth_used;
   v.n_sb = (uint32_t)sb_total;
   v.table = S->table.p;
+  v.nodes = S->nodes.p;
   v.blobs = S->blobs.p;
   v.sbdesc = S->sbdesc.p;
 
@@ -1158,11 +1255,11 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
   I.table_entries = table_total;
   I.leaves = (int64_t)slot_base;
   I.empty_cells = (int64_t)hc[0];
-  I.interior_cells = (int64_t)hc[1];
+  I.interior_cells = (int64_t)hc[1] - (int64_t)hc[2];  // palette overflows became leaves
   I.superbins = sb_total;
   I.leaf_cands = leaf_cands;
   I.leaf_edges = leaf_edges;
-  I.index_bytes = table_total * 4 + blob_total16 * 16 + sb_total * 8;
+  I.index_bytes = top_cells * 4 + n_nodes * 32 + blob_total16 * 16 + sb_total * 8;
   I.max_blob_bytes = max_blob16 * 16;
   I.cell_log2 = g.s0;
   I.fanout_log2 = k;

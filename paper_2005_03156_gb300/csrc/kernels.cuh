@@ -43,6 +43,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 __device__ __forceinline__ void lookup4(const IndexView& ix, const int32_t (&qx)[4],
                                         const int32_t (&qy)[4], const bool (&ok)[4],
                                         uint32_t (&d)[4]) {
+  const uint64_t pol = policy_evict_last();
   uint32_t dx[4], dy[4];
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
@@ -50,19 +51,23 @@ __device__ __forceinline__ void lookup4(const IndexView& ix, const int32_t (&qx)
     dy[j] = (uint32_t)qy[j] - (uint32_t)ix.gy0;
     const uint32_t cx = dx[j] >> ix.s0, cy = dy[j] >> ix.s0;
     const bool in = ok[j] & (cx < ix.nx) & (cy < ix.ny) & (qx[j] >= ix.gx0) & (qy[j] >= ix.gy0);
-    d[j] = in ? __ldg(ix.table + (size_t)cy * ix.nx + cx) : 0u;
+    d[j] = in ? ld_index_u32(ix.table + (size_t)cy * ix.nx + cx, pol) : 0u;
   }
   int s = ix.s0;
-  const uint32_t m = (1u << ix.k) - 1u;
+  const uint32_t m = (1u << NODE_K) - 1u;
 #pragma unroll 1
   while (((d[0] >> 30) == TAG_CHILD) | ((d[1] >> 30) == TAG_CHILD) | ((d[2] >> 30) == TAG_CHILD) |
          ((d[3] >> 30) == TAG_CHILD)) {
-    s -= ix.k;
+    s -= NODE_K;
+    uint4 n0[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)  // issue the node loads of all four points first
+      if ((d[j] >> 30) == TAG_CHILD) n0[j] = ld_index_v4(ix.nodes + 2 * (size_t)(d[j] & PAYLOAD_MASK), pol);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       if ((d[j] >> 30) == TAG_CHILD) {
-        const uint32_t sub = (((dy[j] >> s) & m) << ix.k) | ((dx[j] >> s) & m);
-        d[j] = __ldg(ix.table + (d[j] & PAYLOAD_MASK) + sub);
+        const uint32_t sub = (((dy[j] >> s) & m) << NODE_K) | ((dx[j] >> s) & m);
+        d[j] = node_step(ix.nodes, d[j] & PAYLOAD_MASK, n0[j], sub, pol);
       }
     }
   }

@@ -1,13 +1,17 @@
 // Internal definitions shared by the library's translation units.
 //
 // Layout of a loaded set in HBM (all device-resident, built by index.cu):
-//   table  u32 descriptors: the top grid (row-major, nx * ny) followed by the
-//          child tables of split cells (4^k entries each). A descriptor is
-//          tag:2 | payload:30 with
+//   table  u32 descriptors of the top grid (row-major, nx * ny). A
+//          descriptor is tag:2 | payload:30 with
 //            TAG_EMPTY     no polygon contains any point of the cell  -> -1
 //            TAG_INTERIOR  payload = polygon id answering every point
 //            TAG_LEAF      payload = leaf slot: the crossing test decides
-//            TAG_CHILD     payload = offset of the cell's child table
+//            TAG_CHILD     payload = index of the cell's trie node
+//   nodes  one 32-byte node (one DRAM sector) per split cell, describing its
+//          4 x 4 children: a leaf mask and a child mask (children that are
+//          boundary leaves / split again, numbered from leaf_base /
+//          child_base in child order), and for the other children a 2-bit
+//          code into a 4-entry palette of polygon ids (-1 = empty).
 //   blobs  one 16-byte-aligned record per superbin (32 consecutive leaf
 //          slots), copied to shared memory by one bulk copy:
 //            u32 leaf_start[33]     candidate range of each slot
@@ -45,18 +49,67 @@ __host__ __device__ inline uint32_t make_desc(uint32_t tag, uint32_t payload) {
   return (tag << 30) | (payload & PAYLOAD_MASK);
 }
 
+constexpr int NODE_K = 2;  // a split cell has 2^NODE_K x 2^NODE_K children
+constexpr int NODE_FAN = 1 << (2 * NODE_K);
+
+struct __align__(32) TrieNode {
+  uint32_t masks;       // bits 0-15: leaf children, bits 16-31: split children
+  uint32_t codes;       // 2 bits per child: palette entry of the other children
+  uint32_t leaf_base;   // leaf slot of the first leaf child
+  uint32_t child_base;  // node index of the first split child
+  int32_t pal[4];       // polygon id, or -1 for an empty child
+};
+static_assert(sizeof(TrieNode) == 32, "trie node must be one 32-byte sector");
+
 // Device view of one set's index, passed to kernels by value.
 struct IndexView {
   int32_t gx0, gy0;       // lattice origin of the grid
   uint32_t nx, ny;        // top cells per row / column
   int32_t s0;             // log2 side of a top cell
-  int32_t k;              // log2 children per side of a split cell
   int32_t depth;          // deepest level present
   uint32_t n_sb;          // superbins
-  const uint32_t* table;  // descriptors
+  uint32_t pad;
+  const uint32_t* table;  // top-grid descriptors
+  const uint4* nodes;     // trie nodes, two uint4 per node
   const uint4* blobs;     // superbin records (16-byte units)
   const uint2* sbdesc;    // per superbin: (offset, size) in 16-byte units
 };
+
+// L2 eviction policy for the index: keep it resident while the point stream
+// (loaded and stored with evict-first .cs operations) passes through L2.
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ uint32_t ld_index_u32(const uint32_t* ptr, uint64_t pol) {
+  uint32_t r;
+  asm volatile("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r) : "l"(ptr), "l"(pol));
+  return r;
+}
+
+__device__ __forceinline__ uint4 ld_index_v4(const uint4* ptr, uint64_t pol) {
+  uint4 r;
+  asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+               : "l"(ptr), "l"(pol));
+  return r;
+}
+
+// One trie step: child `sub` of the node whose first half is n0. Returns a
+// descriptor; TAG_CHILD means descend into node `payload`.
+__device__ __forceinline__ uint32_t node_step(const uint4* nodes, uint32_t node, uint4 n0,
+                                              uint32_t sub, uint64_t pol) {
+  const uint32_t bit = 1u << sub, below = bit - 1u;
+  const uint32_t lm = n0.x & 0xFFFFu, cm = n0.x >> 16;
+  if (lm & bit) return make_desc(TAG_LEAF, n0.z + __popc(lm & below));
+  if (cm & bit) return make_desc(TAG_CHILD, n0.w + __popc(cm & below));
+  const uint32_t code = (n0.y >> (2 * sub)) & 3u;
+  const int32_t id = (int32_t)ld_index_u32(
+      reinterpret_cast<const uint32_t*>(nodes + 2 * (size_t)node + 1) + code, pol);
+  return id < 0 ? make_desc(TAG_EMPTY, 0) : make_desc(TAG_INTERIOR, (uint32_t)id);
+}
 
 // Residual entry: a point that fell in a boundary leaf.
 // x = qx, y = qy, z = index of the point within the call (or batch),
@@ -159,14 +212,16 @@ __device__ __forceinline__ uint32_t lookup(const IndexView& ix, int32_t qx, int3
   const uint32_t dy = (uint32_t)qy - (uint32_t)ix.gy0;
   const uint32_t cx = dx >> ix.s0, cy = dy >> ix.s0;
   if (cx >= ix.nx || cy >= ix.ny || qx < ix.gx0 || qy < ix.gy0) return make_desc(TAG_EMPTY, 0);
-  uint32_t d = __ldg(ix.table + (size_t)cy * ix.nx + cx);
+  const uint64_t pol = policy_evict_last();
+  uint32_t d = ld_index_u32(ix.table + (size_t)cy * ix.nx + cx, pol);
   int s = ix.s0;
-  const uint32_t m = (1u << ix.k) - 1u;
+  const uint32_t m = (1u << NODE_K) - 1u;
 #pragma unroll 1
   while ((d >> 30) == TAG_CHILD) {
-    s -= ix.k;
-    const uint32_t sub = (((dy >> s) & m) << ix.k) | ((dx >> s) & m);
-    d = __ldg(ix.table + (d & PAYLOAD_MASK) + sub);
+    s -= NODE_K;
+    const uint32_t node = d & PAYLOAD_MASK;
+    const uint32_t sub = (((dy >> s) & m) << NODE_K) | ((dx >> s) & m);
+    d = node_step(ix.nodes, node, ld_index_v4(ix.nodes + 2 * (size_t)node, pol), sub, pol);
   }
   return d;
 }
@@ -254,6 +309,7 @@ struct pip_set_s {
   int64_t n_vert = 0, n_ring = 0, n_poly = 0;
   // index
   pip::DBuf<uint32_t> table;
+  pip::DBuf<uint4> nodes;
   pip::DBuf<uint4> blobs;
   pip::DBuf<uint2> sbdesc;
   pip::IndexView view{};

@@ -84,8 +84,8 @@ OPTION_CASES = [
     dict(max_depth=-1),                                  # uniform grid
     dict(max_depth=-1, cell_log2=14),                    # fine uniform grid
     dict(max_depth=-1, cell_log2=22),                    # one coarse cell
-    dict(fanout_log2=1, leaf_edges=2, size_ratio=64),    # deep quadtree
-    dict(fanout_log2=3, leaf_edges=4),                   # fanout 64
+    dict(leaf_edges=2, size_ratio=64),                   # deep trie, many palette overflows
+    dict(cell_log2=21, leaf_edges=4, max_depth=8),       # coarse top grid, deep trie
     dict(stage_depth=1, pts_per_cta=7),                  # single stage, tiny items
     dict(stage_depth=2, pts_per_cta=1000),               # items larger than the CTA
     dict(stage_depth=-1, pts_per_cta=300),               # no staging
@@ -251,7 +251,7 @@ def kd_rectangles(rng, box, n):
 
 
 @pytest.mark.parametrize("opts", [None, dict(leaf_edges=1, size_ratio=64), dict(max_depth=-1),
-                                  dict(cell_log2=8, fanout_log2=1)])
+                                  dict(cell_log2=12, max_depth=5)])
 def test_axis_aligned_partition(pipm, opts):
     rng = np.random.default_rng(50)
     box = (1000, 2000, 1000 + 40_000, 2000 + 30_000)
