@@ -763,7 +763,7 @@ static void resolve_opts(const pip_build_opts& in, int64_t n_poly, long long w, 
   o = in;
   if (o.cell_log2 <= 0) {
     const double area = (double)std::max(1ll, w) * (double)std::max(1ll, h);
-    const double target = std::min(std::max(8.0 * (double)n_poly, 4096.0), (double)(1 << 24));
+    const double target = std::min(std::max(32.0 * (double)n_poly, 4096.0), (double)(1 << 24));
     int s = (int)std::lround(std::log2(std::sqrt(area / target)));
     const double cells_cap = (double)(1 << 24);
     while (s < 30 && area / std::ldexp(1.0, 2 * s) > cells_cap) ++s;
@@ -773,10 +773,10 @@ static void resolve_opts(const pip_build_opts& in, int64_t n_poly, long long w, 
   if (o.max_depth == 0) o.max_depth = std::max(0, std::min(8, (o.cell_log2 - 6) / o.fanout_log2));
   else if (o.max_depth < 0) o.max_depth = 0;  // uniform grid
   o.max_depth = std::min(o.max_depth, std::max(0, (o.cell_log2 - 1) / o.fanout_log2));
-  if (o.leaf_edges <= 0) o.leaf_edges = 16;
+  if (o.leaf_edges <= 0) o.leaf_edges = 8;
   if (o.size_ratio == 0) o.size_ratio = 16;
   if (o.pts_per_cta <= 0) o.pts_per_cta = 256;
-  if (o.stage_depth == 0) o.stage_depth = 2;
+  if (o.stage_depth == 0) o.stage_depth = -1;  // measured best when chunks span many superbins
   if (o.stage_depth < 0) o.stage_depth = -1;  // no shared-memory staging
   if (o.stage_depth > 2) o.stage_depth = 2;
   if (o.cand_mode <= 0) o.cand_mode = n_levels > 0 ? 1 : 2;

@@ -59,15 +59,15 @@ __device__ __forceinline__ void lookup4(const IndexView& ix, const int32_t (&qx)
   while (((d[0] >> 30) == TAG_CHILD) | ((d[1] >> 30) == TAG_CHILD) | ((d[2] >> 30) == TAG_CHILD) |
          ((d[3] >> 30) == TAG_CHILD)) {
     s -= NODE_K;
-    uint4 n0[4];
+    NodeWords nw[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j)  // issue the node loads of all four points first
-      if ((d[j] >> 30) == TAG_CHILD) n0[j] = ld_index_v4(ix.nodes + 2 * (size_t)(d[j] & PAYLOAD_MASK), pol);
+      if ((d[j] >> 30) == TAG_CHILD) nw[j] = ld_node(ix.nodes, d[j] & PAYLOAD_MASK, pol);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       if ((d[j] >> 30) == TAG_CHILD) {
         const uint32_t sub = (((dy[j] >> s) & m) << NODE_K) | ((dx[j] >> s) & m);
-        d[j] = node_step(ix.nodes, d[j] & PAYLOAD_MASK, n0[j], sub, pol);
+        d[j] = node_step(nw[j], sub);
       }
     }
   }

@@ -97,17 +97,29 @@ __device__ __forceinline__ uint4 ld_index_v4(const uint4* ptr, uint64_t pol) {
   return r;
 }
 
-// One trie step: child `sub` of the node whose first half is n0. Returns a
-// descriptor; TAG_CHILD means descend into node `payload`.
-__device__ __forceinline__ uint32_t node_step(const uint4* nodes, uint32_t node, uint4 n0,
-                                              uint32_t sub, uint64_t pol) {
+// A whole 32-byte node in one 256-bit load (one sector, one request).
+struct NodeWords {
+  uint32_t w[8];
+};
+
+__device__ __forceinline__ NodeWords ld_node(const uint4* nodes, uint32_t node, uint64_t pol) {
+  NodeWords n;
+  asm volatile("ld.global.nc.L2::cache_hint.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8], %9;"
+               : "=r"(n.w[0]), "=r"(n.w[1]), "=r"(n.w[2]), "=r"(n.w[3]), "=r"(n.w[4]), "=r"(n.w[5]),
+                 "=r"(n.w[6]), "=r"(n.w[7])
+               : "l"(nodes + 2 * (size_t)node), "l"(pol));
+  return n;
+}
+
+// One trie step: child `sub` of node n. Returns a descriptor; TAG_CHILD
+// means descend into node `payload`.
+__device__ __forceinline__ uint32_t node_step(const NodeWords& n, uint32_t sub) {
   const uint32_t bit = 1u << sub, below = bit - 1u;
-  const uint32_t lm = n0.x & 0xFFFFu, cm = n0.x >> 16;
-  if (lm & bit) return make_desc(TAG_LEAF, n0.z + __popc(lm & below));
-  if (cm & bit) return make_desc(TAG_CHILD, n0.w + __popc(cm & below));
-  const uint32_t code = (n0.y >> (2 * sub)) & 3u;
-  const int32_t id = (int32_t)ld_index_u32(
-      reinterpret_cast<const uint32_t*>(nodes + 2 * (size_t)node + 1) + code, pol);
+  const uint32_t lm = n.w[0] & 0xFFFFu, cm = n.w[0] >> 16;
+  if (lm & bit) return make_desc(TAG_LEAF, n.w[2] + __popc(lm & below));
+  if (cm & bit) return make_desc(TAG_CHILD, n.w[3] + __popc(cm & below));
+  const uint32_t code = (n.w[1] >> (2 * sub)) & 3u;
+  const int32_t id = (int32_t)(code == 0 ? n.w[4] : code == 1 ? n.w[5] : code == 2 ? n.w[6] : n.w[7]);
   return id < 0 ? make_desc(TAG_EMPTY, 0) : make_desc(TAG_INTERIOR, (uint32_t)id);
 }
 
@@ -221,7 +233,7 @@ __device__ __forceinline__ uint32_t lookup(const IndexView& ix, int32_t qx, int3
     s -= NODE_K;
     const uint32_t node = d & PAYLOAD_MASK;
     const uint32_t sub = (((dy >> s) & m) << NODE_K) | ((dx >> s) & m);
-    d = node_step(ix.nodes, node, ld_index_v4(ix.nodes + 2 * (size_t)node, pol), sub, pol);
+    d = node_step(ld_node(ix.nodes, node, pol), sub);
   }
   return d;
 }

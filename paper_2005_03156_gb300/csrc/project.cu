@@ -37,7 +37,7 @@ __device__ __forceinline__ void load4(const double* __restrict__ lon, const doub
 // the current step's trie walk, so the stream's DRAM latency overlaps the
 // dependent lookups.
 template <bool VEC>
-__global__ void __launch_bounds__(K1_THREADS, 4) k_classify_points(
+__global__ void __launch_bounds__(K1_THREADS, 3) k_classify_points(
     IndexView ix, const double* __restrict__ lon, const double* __restrict__ lat, int64_t n,
     int32_t* __restrict__ out, Residual* __restrict__ queue, uint32_t* __restrict__ qcount,
     uint32_t* __restrict__ hist) {
