@@ -203,6 +203,12 @@ pip_status pip_plan_run(pip_plan plan, const pip_query* q, int32_t n_q, void* st
 pip_status pip_plan_check(pip_plan plan, void* stream);
 pip_status pip_plan_destroy(pip_plan plan);
 
+/* Autotuner for a plan: time runs of q[0..n_q) with points per crossing
+ * item in {128, 256, 512, 1024} and staging off / on, keep the fastest
+ * (written to *pts_per_cta and *staged when not NULL). Synchronous. */
+pip_status pip_plan_tune(pip_plan plan, const pip_query* q, int32_t n_q, void* stream,
+                         int32_t* pts_per_cta, int32_t* staged);
+
 /* One-shot convenience: create a plan, run, destroy (synchronous). */
 pip_status pip_project_batch(const pip_query* q, int32_t n_q, void* stream);
 

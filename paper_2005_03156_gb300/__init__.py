@@ -225,6 +225,13 @@ class Plan:
     def check(self, stream=None):
         _native.check(lib().pip_plan_check(self.handle, _stream(stream)))
 
+    def tune(self, qs, stream=None):
+        arr, keep = _queries(qs)
+        ppc, st = ctypes.c_int32(0), ctypes.c_int32(0)
+        _native.check(lib().pip_plan_tune(self.handle, arr, len(qs), _stream(stream),
+                                          ctypes.byref(ppc), ctypes.byref(st)))
+        return {"pts_per_cta": ppc.value, "staged": st.value}
+
     def destroy(self):
         if self.handle and self.handle.value:
             _native.check(lib().pip_plan_destroy(self.handle))

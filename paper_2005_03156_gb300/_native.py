@@ -81,6 +81,7 @@ SIGNATURES = {
     "pip_plan_check": (I32, [P, P]),
     "pip_plan_destroy": (I32, [P]),
     "pip_project_batch": (I32, [P, I32, P]),
+    "pip_plan_tune": (I32, [P, P, I32, P, P, P]),
     "pip_set_tune": (I32, [P, P, P, I64, P, P]),
     "pip_server_create": (I32, [P, I32, P, P]),
     "pip_server_submit": (I32, [P, I32, P, P, I64, P, P]),

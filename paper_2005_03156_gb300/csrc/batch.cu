@@ -1,0 +1,606 @@
+// Batched form: many uneven queries over many resident sets in one
+// persistent, work-stealing, cooperative launch captured in a CUDA graph.
+//
+// Phases of the one kernel, separated by grid-wide barriers (bounded waits:
+// a barrier that does not complete within 2 s sets the status word and the
+// kernel runs to its end without further waiting):
+//   0 classify   CTAs take 4096-point tiles from an atomic counter; each
+//                point is quantized, looked up in its query's set trie and
+//                either answered (EMPTY / INTERIOR) or appended to the
+//                residual queue with a global slot (set base + leaf slot).
+//   1 scan       exclusive scan of the per-superbin counts of all sets.
+//   2 scatter    counting sort of the residual by global superbin.
+//   3 cross      CTAs take chunks of pts_per_cta binned points; a chunk whose
+//                points all belong to one set and whose records fit a stage
+//                is staged with one cp.async.bulk copy; then the exact
+//                crossing test runs per point and the id is written to its
+//                query's output.
+// The results equal separate plain projections bit for bit: same index,
+// same arithmetic, same rule.
+#include <algorithm>
+#include <cstring>
+#include <memory>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace pip {
+
+constexpr int B_THREADS = 256;
+constexpr int TILE = 4096;
+constexpr int MAX_SETS = 64;
+
+struct DevSet {
+  IndexView view;
+  uint32_t sb_base;  // first global superbin of the set
+  uint32_t pad[3];
+};
+
+struct DevQuery {
+  const double* lon;
+  const double* lat;
+  int32_t* out;
+  uint32_t set;
+  uint32_t n;
+};
+
+// Layout of the per-run table block (host pinned -> device in one copy).
+struct RunHeader {
+  uint32_t n_q, n_sets, n_tiles, total_points;
+  uint32_t n_sb_total, ppc, stage16, pad;
+};
+
+struct PlanBufs {
+  RunHeader* hdr;         // header
+  DevSet* sets;           // [MAX_SETS]
+  DevQuery* queries;      // [max_queries]
+  uint32_t* qoff;         // [max_queries + 1] point offsets
+  uint4* tiles;           // [max_tiles] (query, start, count, global offset)
+  Residual* queue;        // [max_points]
+  Residual* binned;       // [max_points]
+  uint32_t* hist;         // [sb_cap] counts
+  uint32_t* cursor;       // [sb_cap]
+  uint64_t* off;          // [sb_cap]
+  uint64_t* partial;      // [grid + 1]
+  uint32_t* ctr;          // [0] qcount [1] tile ctr [2] chunk ctr [3] barrier count [4] barrier gen
+  uint32_t* status;       // bounded-wait status word
+};
+
+__device__ __forceinline__ void grid_barrier(const PlanBufs& B, uint32_t nblocks) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile uint32_t* vgen = B.ctr + 4;
+    const uint32_t g = *vgen;
+    __threadfence();
+    if (atomicAdd(B.ctr + 3, 1u) == nblocks - 1) {
+      B.ctr[3] = 0;
+      __threadfence();
+      atomicAdd(B.ctr + 4, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (*vgen == g) {
+        if (global_ns() - t0 > WAIT_NS) {
+          atomicOr(B.status, 2u);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+struct BatchStore {
+  const uint32_t* qoff;
+  const DevQuery* queries;
+  uint32_t n_q;
+  __device__ __forceinline__ void operator()(const Residual& r, int32_t id) const {
+    // query holding global point r.z: last q with qoff[q] <= r.z
+    uint32_t lo = 0, hi = n_q;
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (qoff[mid] <= r.z) lo = mid; else hi = mid;
+    }
+    queries[lo].out[r.z - qoff[lo]] = id;
+  }
+};
+
+// Set of a global slot (sets in increasing sb_base order).
+__device__ __forceinline__ uint32_t set_of_slot(const DevSet* sets, uint32_t n_sets, uint32_t gslot) {
+  const uint32_t gsb = gslot >> SB_LOG2;
+  uint32_t s = 0;
+  while (s + 1 < n_sets && sets[s + 1].sb_base <= gsb) ++s;
+  return s;
+}
+
+// Crossing test of one chunk whose points may span several sets.
+__device__ __forceinline__ void batch_test_chunk(const DevSet* sets, uint32_t n_sets,
+                                                 const Residual* __restrict__ binned, uint32_t first,
+                                                 uint32_t count, const uint4* staged, uint32_t region16,
+                                                 BatchStore store) {
+  const int lane = threadIdx.x & 31;
+  for (uint32_t base = threadIdx.x & ~31u; base < count; base += blockDim.x) {
+    const uint32_t t = base + lane;
+    const bool active = t < count;
+    Residual r = make_uint4(0, 0, 0, 0);
+    const uint4* bp = nullptr;
+    if (active) {
+      r = binned[first + t];
+      const DevSet& S = sets[set_of_slot(sets, n_sets, r.w)];
+      const uint2 sd = S.view.sbdesc[(r.w >> SB_LOG2) - S.sb_base];
+      bp = staged ? staged + (sd.x - region16) : S.view.blobs + sd.x;
+    }
+    BlobView b{nullptr, nullptr};
+    if (active) b = blob_view(bp);
+    const uint32_t local = r.w & (SB_SLOTS - 1);
+    const bool is_long = active && leaf_edges(b, local) > (uint32_t)LONG_LIST;
+    int32_t id = -1;
+    if (active && !is_long) id = test_point(b, local, (int32_t)r.x, (int32_t)r.y);
+    uint32_t lm = __ballot_sync(0xffffffffu, is_long);
+    while (lm) {
+      const int j = __ffs(lm) - 1;
+      lm &= lm - 1;
+      const int32_t px = (int32_t)__shfl_sync(0xffffffffu, r.x, j);
+      const int32_t py = (int32_t)__shfl_sync(0xffffffffu, r.y, j);
+      const uint32_t lj = __shfl_sync(0xffffffffu, local, j);
+      const unsigned long long pj = __shfl_sync(0xffffffffu, (unsigned long long)(uintptr_t)bp, j);
+      const int32_t v = test_point_warp(blob_view((const uint4*)(uintptr_t)pj), lj, px, py);
+      if (lane == j) id = v;
+    }
+    if (active) store(r, id);
+  }
+}
+
+template <int STAGED>
+__global__ void __launch_bounds__(B_THREADS) k_batch(PlanBufs B) {
+  extern __shared__ __align__(128) uint4 stage_mem[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t s_w, s_staged, s_region;
+  __shared__ DevSet s_sets[MAX_SETS];
+  __shared__ uint64_t s_scan[B_THREADS / 32];
+  const uint32_t nblocks = gridDim.x;
+  const RunHeader H = *B.hdr;
+  for (uint32_t i = threadIdx.x; i < H.n_sets * (sizeof(DevSet) / 4); i += blockDim.x)
+    reinterpret_cast<uint32_t*>(s_sets)[i] = reinterpret_cast<const uint32_t*>(B.sets)[i];
+  if (STAGED && threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+
+  // ---- phase 0: classify tiles
+  while (true) {
+    if (threadIdx.x == 0) s_w = atomicAdd(B.ctr + 1, 1u);
+    __syncthreads();
+    const uint32_t w = s_w;
+    __syncthreads();
+    if (w >= H.n_tiles) break;
+    const uint4 tl = B.tiles[w];  // (query, start, count, global offset)
+    const DevQuery q = B.queries[tl.x];
+    const DevSet& S = s_sets[q.set];
+    const uint32_t slot_add = S.sb_base << SB_LOG2;
+    for (uint32_t g0 = 0; g0 < tl.z; g0 += 4 * blockDim.x) {
+      const uint32_t j0 = g0 + 4 * threadIdx.x;  // offset within the tile
+      double x[4], y[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const bool have = j0 + j < tl.z;
+        x[j] = have ? __ldcs(q.lon + tl.y + j0 + j) : __longlong_as_double(0x7FF8000000000000ll);
+        y[j] = have ? __ldcs(q.lat + tl.y + j0 + j) : 0.0;
+      }
+      int32_t id[4], qx[4], qy[4];
+      uint32_t d[4];
+      const uint32_t mask = classify4(S.view, x, y, id, qx, qy, d);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (j0 + j < tl.z) q.out[tl.y + j0 + j] = id[j];
+      append_residual(mask, qx, qy, d, tl.w + j0, B.queue, B.ctr + 0, B.hist, slot_add);
+    }
+  }
+  grid_barrier(B, nblocks);
+
+  // ---- phase 1: exclusive scan of hist[0, n_sb_total) over all CTAs
+  const uint32_t nsb = H.n_sb_total;
+  const uint32_t seg = (nsb + nblocks - 1) / nblocks;
+  const uint32_t a = min(nsb, blockIdx.x * seg), e = min(nsb, a + seg);
+  {
+    uint64_t part = 0;
+    for (uint32_t i = a + threadIdx.x; i < e; i += blockDim.x) part += B.hist[i];
+    for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) s_scan[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint64_t t = 0;
+      for (int i = 0; i < B_THREADS / 32; ++i) t += s_scan[i];
+      B.partial[blockIdx.x] = t;
+    }
+  }
+  grid_barrier(B, nblocks);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    uint64_t run = 0;
+    for (uint32_t c = 0; c < nblocks; ++c) {
+      const uint64_t v = B.partial[c];
+      B.partial[c] = run;
+      run += v;
+    }
+  }
+  grid_barrier(B, nblocks);
+  {  // block-wide scan of this CTA's segment, blockDim values per step
+    uint64_t run = B.partial[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t base = a; base < e; base += blockDim.x) {
+      const uint32_t i = base + threadIdx.x;
+      const uint64_t v = i < e ? B.hist[i] : 0;
+      uint64_t incl = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      if (lane == 31) s_scan[warp] = incl;
+      __syncthreads();
+      uint64_t wbase = 0, total = 0;
+      for (int k = 0; k < B_THREADS / 32; ++k) {
+        if (k < warp) wbase += s_scan[k];
+        total += s_scan[k];
+      }
+      if (i < e) B.off[i] = run + wbase + incl - v;
+      run += total;
+      __syncthreads();
+    }
+  }
+  grid_barrier(B, nblocks);
+
+  // ---- phase 2: scatter by global superbin
+  const uint32_t n_res = *(volatile uint32_t*)(B.ctr + 0);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_res; i += nblocks * blockDim.x) {
+    const Residual r = B.queue[i];
+    const uint32_t gsb = r.w >> SB_LOG2;
+    B.binned[(uint32_t)B.off[gsb] + atomicAdd(B.cursor + gsb, 1u)] = r;
+  }
+  grid_barrier(B, nblocks);
+
+  // ---- phase 3: crossing tests, chunks of ppc binned points
+  const uint32_t ppc = H.ppc;
+  const uint32_t n_items = (n_res + ppc - 1) / ppc;
+  const BatchStore store{B.qoff, B.queries, H.n_q};
+  uint32_t phase = 0;
+  while (true) {
+    if (threadIdx.x == 0) {
+      const uint32_t w = atomicAdd(B.ctr + 2, 1u);
+      s_w = w;
+      s_staged = 0;
+      if (STAGED && w < n_items) {
+        const uint32_t first = w * ppc, last = min(first + ppc, n_res) - 1;
+        const uint32_t ga = B.binned[first].w, gb = B.binned[last].w;
+        const uint32_t sa = set_of_slot(s_sets, H.n_sets, ga), sb = set_of_slot(s_sets, H.n_sets, gb);
+        if (sa == sb) {
+          const DevSet& S = s_sets[sa];
+          const uint2 da = S.view.sbdesc[(ga >> SB_LOG2) - S.sb_base];
+          const uint2 db = S.view.sbdesc[(gb >> SB_LOG2) - S.sb_base];
+          const uint32_t len16 = db.x + db.y - da.x;
+          if (len16 <= H.stage16) {
+            fence_proxy_async();
+            bulk_load(stage_mem, S.view.blobs + da.x, len16 * 16u, &bar);
+            s_staged = 1;
+            s_region = da.x;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    const uint32_t w = s_w;
+    if (w >= n_items) break;
+    const uint4* staged = nullptr;
+    if (STAGED && s_staged) {
+      if (!mbar_wait(&bar, phase)) atomicOr(B.status, 1u);
+      phase ^= 1u;
+      staged = stage_mem;
+    }
+    const uint32_t first = w * ppc;
+    batch_test_chunk(s_sets, H.n_sets, B.binned, first, min(ppc, n_res - first), staged, s_region,
+                     store);
+    __syncthreads();
+  }
+}
+
+}  // namespace pip
+
+using namespace pip;
+
+struct pip_plan_s {
+  int device = 0;
+  int64_t max_points = 0;
+  int32_t max_queries = 0;
+  int64_t max_tiles = 0;
+  int64_t sb_cap = 0;
+  int grid = 0;
+  int staged = 0;      // 0 unstaged, 1 staged
+  uint32_t ppc = 256;
+  uint32_t stage_bytes = 48 * 1024;
+  Alloc alloc;
+  DBuf<uint8_t> tables;  // header | sets | queries | qoff | tiles
+  size_t tables_bytes = 0;
+  DBuf<Residual> queue, binned;
+  DBuf<uint32_t> hist;   // counts | cursors
+  DBuf<uint64_t> off, partial;
+  DBuf<uint32_t> ctr, status;
+  // two pinned table buffers and two graphs: the host fills one while the
+  // previous run's graph may still be copying the other
+  uint8_t* host_tables[2] = {nullptr, nullptr};
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaEvent_t done[2] = {nullptr, nullptr};
+  bool used[2] = {false, false};
+  int turn = 0;
+  PlanBufs bufs{};
+  size_t off_sets = 0, off_q = 0, off_qoff = 0, off_tiles = 0;
+  void drop_graphs() {
+    for (int i = 0; i < 2; ++i) {
+      if (exec[i]) cudaGraphExecDestroy(exec[i]);
+      if (graph[i]) cudaGraphDestroy(graph[i]);
+      exec[i] = nullptr;
+      graph[i] = nullptr;
+    }
+  }
+  ~pip_plan_s() {
+    drop_graphs();
+    for (int i = 0; i < 2; ++i) {
+      if (host_tables[i]) cudaFreeHost(host_tables[i]);
+      if (done[i]) cudaEventDestroy(done[i]);
+    }
+  }
+};
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+static pip_status plan_alloc_sb(pip_plan_s* P, int64_t need, cudaStream_t s) {
+  if (need <= P->sb_cap) return PIP_OK;
+  const int64_t cap = std::max<int64_t>(need, 2 * P->sb_cap);
+  if (!P->hist.alloc(&P->alloc, 2 * cap + 2, s) || !P->off.alloc(&P->alloc, cap + 1, s))
+    return fail(PIP_ENOMEM, "pip_plan: superbin buffers");
+  P->sb_cap = cap;
+  P->drop_graphs();  // buffers moved: capture again
+  return PIP_OK;
+}
+
+static int batch_smem(int staged, uint32_t stage_bytes) { return staged ? (int)stage_bytes : 0; }
+
+static pip_status plan_grid(pip_plan_s* P) {
+  int occ = 0;
+  const int smem = batch_smem(P->staged, P->stage_bytes);
+  if (P->staged) {
+    PIP_CUDA(cudaFuncSetAttribute(k_batch<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    PIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<1>, B_THREADS, smem));
+  } else {
+    PIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<0>, B_THREADS, 0));
+  }
+  if (occ < 1) return fail(PIP_ECUDA, "pip_plan: batched kernel does not fit an SM");
+  P->grid = num_sms() * occ;
+  return PIP_OK;
+}
+
+// Capture: table copy -> memsets of the counters -> cooperative kernel.
+static pip_status plan_capture(pip_plan_s* P, int t, cudaStream_t s) {
+  if (P->exec[t]) return PIP_OK;
+  cudaStream_t cs;
+  PIP_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  pip_status res = PIP_OK;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaMemcpyAsync(P->tables.p, P->host_tables[t], P->tables_bytes, cudaMemcpyHostToDevice, cs);
+    cudaMemsetAsync(P->ctr.p, 0, 8 * sizeof(uint32_t), cs);
+    cudaMemsetAsync(P->hist.p, 0, (2 * P->sb_cap + 2) * sizeof(uint32_t), cs);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)P->grid);
+    cfg.blockDim = dim3(B_THREADS);
+    cfg.dynamicSmemBytes = (size_t)batch_smem(P->staged, P->stage_bytes);
+    cfg.stream = cs;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (P->staged)
+      e = cudaLaunchKernelEx(&cfg, k_batch<1>, P->bufs);
+    else
+      e = cudaLaunchKernelEx(&cfg, k_batch<0>, P->bufs);
+    cudaError_t e2 = cudaStreamEndCapture(cs, &P->graph[t]);
+    if (e != cudaSuccess) res = cuda_fail(e, "pip_plan: cooperative launch capture");
+    else if (e2 != cudaSuccess) res = cuda_fail(e2, "pip_plan: end capture");
+    else {
+      e = cudaGraphInstantiate(&P->exec[t], P->graph[t], 0);
+      if (e != cudaSuccess) res = cuda_fail(e, "pip_plan: graph instantiate");
+    }
+  } else {
+    res = cuda_fail(e, "pip_plan: begin capture");
+  }
+  cudaStreamDestroy(cs);
+  (void)s;
+  return res;
+}
+
+extern "C" pip_status pip_plan_create(int64_t max_points, int32_t max_queries, void* stream,
+                                      pip_plan* out) {
+  if (!out) return fail(PIP_EINVAL, "pip_plan_create: out is NULL");
+  *out = nullptr;
+  if (max_points <= 0 || max_points >= (1ll << 32) - 1 || max_queries <= 0)
+    return fail(PIP_EINVAL, "pip_plan_create: 0 < max_points < 2^32 - 1 and max_queries > 0");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::unique_ptr<pip_plan_s> P(new pip_plan_s());
+  PIP_CUDA(cudaGetDevice(&P->device));
+  P->max_points = max_points;
+  P->max_queries = max_queries;
+  P->max_tiles = max_points / TILE + max_queries + 1;
+  P->off_sets = align_up(sizeof(RunHeader), 256);
+  P->off_q = align_up(P->off_sets + sizeof(DevSet) * MAX_SETS, 256);
+  P->off_qoff = align_up(P->off_q + sizeof(DevQuery) * (size_t)max_queries, 256);
+  P->off_tiles = align_up(P->off_qoff + sizeof(uint32_t) * ((size_t)max_queries + 1), 256);
+  P->tables_bytes = align_up(P->off_tiles + sizeof(uint4) * (size_t)P->max_tiles, 256);
+  Alloc* al = &P->alloc;
+  if (!P->tables.alloc(al, P->tables_bytes, s) || !P->queue.alloc(al, max_points, s) ||
+      !P->binned.alloc(al, max_points, s) || !P->ctr.alloc(al, 8, s) || !P->status.alloc(al, 2, s))
+    return fail(PIP_ENOMEM, "pip_plan_create: device buffers");
+  for (int i = 0; i < 2; ++i) {
+    PIP_CUDA(cudaMallocHost((void**)&P->host_tables[i], P->tables_bytes));
+    std::memset(P->host_tables[i], 0, P->tables_bytes);
+    PIP_CUDA(cudaEventCreateWithFlags(&P->done[i], cudaEventDisableTiming));
+  }
+  PIP_CUDA(cudaMemsetAsync(P->status.p, 0, 2 * sizeof(uint32_t), s));
+  pip_status st = plan_alloc_sb(P.get(), 1 << 16, s);
+  if (st != PIP_OK) return st;
+  st = plan_grid(P.get());
+  if (st != PIP_OK) return st;
+  if (!P->partial.alloc(al, (size_t)P->grid + 1, s)) return fail(PIP_ENOMEM, "pip_plan_create: partials");
+  PIP_CUDA(cudaStreamSynchronize(s));
+  *out = P.release();
+  return PIP_OK;
+}
+
+static void plan_fill_bufs(pip_plan_s* P) {
+  PlanBufs& B = P->bufs;
+  uint8_t* t = P->tables.p;
+  B.hdr = (RunHeader*)t;
+  B.sets = (DevSet*)(t + P->off_sets);
+  B.queries = (DevQuery*)(t + P->off_q);
+  B.qoff = (uint32_t*)(t + P->off_qoff);
+  B.tiles = (uint4*)(t + P->off_tiles);
+  B.queue = P->queue.p;
+  B.binned = P->binned.p;
+  B.hist = P->hist.p;
+  B.cursor = P->hist.p + P->sb_cap;
+  B.off = P->off.p;
+  B.partial = P->partial.p;
+  B.ctr = P->ctr.p;
+  B.status = P->status.p;
+}
+
+extern "C" pip_status pip_plan_run(pip_plan plan, const pip_query* q, int32_t n_q, void* stream) {
+  if (!plan) return fail(PIP_EINVAL, "pip_plan_run: NULL plan");
+  if (n_q < 0 || n_q > plan->max_queries) return fail(PIP_EINVAL, "pip_plan_run: too many queries");
+  if (n_q > 0 && !q) return fail(PIP_EINVAL, "pip_plan_run: NULL queries");
+  cudaStream_t s = (cudaStream_t)stream;
+  // distinct sets in order of first use
+  std::vector<pip_set> sets;
+  std::vector<uint32_t> qset(n_q);
+  int64_t total = 0;
+  for (int i = 0; i < n_q; ++i) {
+    if (!q[i].set || q[i].n < 0) return fail(PIP_EINVAL, "pip_plan_run: bad query");
+    if (q[i].n > 0 && (!q[i].lon || !q[i].lat || !q[i].out))
+      return fail(PIP_EINVAL, "pip_plan_run: NULL query array");
+    auto it = std::find(sets.begin(), sets.end(), q[i].set);
+    if (it == sets.end()) {
+      if ((int)sets.size() == MAX_SETS) return fail(PIP_EINVAL, "pip_plan_run: more than 64 sets");
+      sets.push_back(q[i].set);
+      it = sets.end() - 1;
+    }
+    qset[i] = (uint32_t)(it - sets.begin());
+    total += q[i].n;
+  }
+  if (total > plan->max_points) return fail(PIP_EINVAL, "pip_plan_run: more points than max_points");
+  int64_t sb_total = 0;
+  std::vector<uint32_t> sb_base(sets.size());
+  for (size_t i = 0; i < sets.size(); ++i) {
+    sb_base[i] = (uint32_t)sb_total;
+    sb_total += std::max<int64_t>(1, sets[i]->view.n_sb);
+  }
+  if ((sb_total << SB_LOG2) >= (1ll << 32)) return fail(PIP_ERANGE, "pip_plan_run: too many leaf slots");
+  pip_status st = plan_alloc_sb(plan, sb_total + 1, s);
+  if (st != PIP_OK) return st;
+  // tables into pinned host memory (the buffer of this turn, once its last
+  // run has finished reading it)
+  const int t = plan->turn;
+  if (plan->used[t]) PIP_CUDA(cudaEventSynchronize(plan->done[t]));
+  RunHeader H{};
+  uint8_t* h = plan->host_tables[t];
+  DevSet* hs = (DevSet*)(h + plan->off_sets);
+  for (size_t i = 0; i < sets.size(); ++i) {
+    hs[i].view = sets[i]->view;
+    hs[i].sb_base = sb_base[i];
+  }
+  DevQuery* hq = (DevQuery*)(h + plan->off_q);
+  uint32_t* hqoff = (uint32_t*)(h + plan->off_qoff);
+  uint4* ht = (uint4*)(h + plan->off_tiles);
+  uint32_t n_tiles = 0, acc = 0;
+  for (int i = 0; i < n_q; ++i) {
+    hq[i] = DevQuery{q[i].lon, q[i].lat, q[i].out, qset[i], (uint32_t)q[i].n};
+    hqoff[i] = acc;
+    for (int64_t t0 = 0; t0 < q[i].n; t0 += TILE)
+      ht[n_tiles++] = make_uint4((uint32_t)i, (uint32_t)t0, (uint32_t)std::min<int64_t>(TILE, q[i].n - t0),
+                                 acc + (uint32_t)t0);
+    acc += (uint32_t)q[i].n;
+  }
+  hqoff[n_q] = acc;
+  H.n_q = (uint32_t)n_q;
+  H.n_sets = (uint32_t)sets.size();
+  H.n_tiles = n_tiles;
+  H.total_points = acc;
+  H.n_sb_total = (uint32_t)sb_total;
+  H.ppc = plan->ppc;
+  H.stage16 = plan->stage_bytes / 16;
+  std::memcpy(h, &H, sizeof(H));
+  plan_fill_bufs(plan);
+  st = plan_capture(plan, t, s);
+  if (st != PIP_OK) return st;
+  PIP_CUDA(cudaGraphLaunch(plan->exec[t], s));
+  PIP_CUDA(cudaEventRecord(plan->done[t], s));
+  plan->used[t] = true;
+  plan->turn = t ^ 1;
+  count_launches(1);
+  return PIP_OK;
+}
+
+extern "C" pip_status pip_plan_check(pip_plan plan, void* stream) {
+  if (!plan) return fail(PIP_EINVAL, "pip_plan_check: NULL plan");
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t w = 0;
+  PIP_CUDA(cudaMemcpyAsync(&w, plan->status.p, sizeof(w), cudaMemcpyDeviceToHost, s));
+  PIP_CUDA(cudaStreamSynchronize(s));
+  if (w) {
+    PIP_CUDA(cudaMemsetAsync(plan->status.p, 0, sizeof(uint32_t), s));
+    PIP_CUDA(cudaStreamSynchronize(s));
+    return fail(PIP_ETIMEOUT, w & 2u ? "batched launch: a grid barrier wait ran out"
+                                     : "batched launch: a staging wait ran out");
+  }
+  return PIP_OK;
+}
+
+extern "C" pip_status pip_plan_destroy(pip_plan plan) {
+  if (!plan) return PIP_OK;
+  cudaDeviceSynchronize();
+  delete plan;
+  return PIP_OK;
+}
+
+// Plan knobs used by the autotuner (internal).
+namespace pip {
+pip_status plan_set_knobs(pip_plan plan, uint32_t ppc, int staged) {
+  if (plan->ppc == ppc && plan->staged == staged) return PIP_OK;
+  plan->ppc = ppc;
+  plan->drop_graphs();  // the header carries ppc, but the graph holds the launch shape
+  if (plan->staged != staged) {
+    plan->staged = staged;
+    pip_status st = plan_grid(plan);
+    if (st != PIP_OK) return st;
+    if (!plan->partial.alloc(&plan->alloc, (size_t)plan->grid + 1, 0))
+      return fail(PIP_ENOMEM, "pip_plan: partials");
+    cudaDeviceSynchronize();
+  }
+  return PIP_OK;
+}
+}  // namespace pip
+
+extern "C" pip_status pip_project_batch(const pip_query* q, int32_t n_q, void* stream) {
+  if (n_q < 0 || (n_q > 0 && !q)) return fail(PIP_EINVAL, "pip_project_batch: bad arguments");
+  if (n_q == 0) return PIP_OK;
+  int64_t total = 0;
+  for (int i = 0; i < n_q; ++i) total += std::max<int64_t>(0, q[i].n);
+  pip_plan plan = nullptr;
+  pip_status st = pip_plan_create(std::max<int64_t>(1, total), n_q, stream, &plan);
+  if (st != PIP_OK) return st;
+  st = pip_plan_run(plan, q, n_q, stream);
+  if (st == PIP_OK) st = pip_plan_check(plan, stream);
+  pip_plan_destroy(plan);
+  return st;
+}
