@@ -176,6 +176,26 @@ pip_status pip_project(pip_set set, const double* lon, const double* lat, int64_
 pip_status pip_project_ex(pip_set set, const double* lon, const double* lat, int64_t n,
                           int32_t* out, void* stream, pip_project_stats* stats);
 
+/* pip_project for callers that cannot allocate device memory during the
+ * call. The paper has no counterpart: it is an addition for embedding the
+ * join where an allocation is not allowed or not affordable at call time,
+ * e.g. code recorded into a CUDA stream capture that must not allocate,
+ * latency-critical serving paths where a pool miss or an out-of-memory
+ * failure mid-request is unacceptable, and processes that reserve all their
+ * device memory up front. lon, lat, out are device pointers; n <= 262144
+ * points per call and the set may have at most 524288 superbins
+ * (PIP_EINVAL otherwise). The scratch is one fixed device array of about
+ * 16 MB inside the library: every GPU context that loads the library holds
+ * it until the process exits, whether or not this call is used. The first
+ * call on a device looks up that array's device address; make that first
+ * call before any stream capture. All calls share the array and it keeps
+ * the last call's contents (the call clears what must start at zero), so
+ * calls that overlap on the GPU race: serialise them (one stream, or
+ * synchronise between calls). Asynchronous on `stream`; results are the
+ * same as pip_project's. */
+pip_status pip_project_noalloc(pip_set set, const double* lon, const double* lat, int64_t n,
+                               int32_t* out, void* stream);
+
 /* Device error word of the set (a bounded device wait that ran out sets it):
  * synchronises `stream`, returns PIP_OK or PIP_ETIMEOUT and clears it. */
 pip_status pip_set_check(pip_set set, void* stream);

@@ -168,6 +168,15 @@ def pip_project_ex(s: PolygonSet, lon, lat, out=None, stream=None):
     return out, {"n": st.n, "residual": st.residual, "items": st.items}
 
 
+def pip_project_noalloc(s: PolygonSet, lon, lat, out, stream=None):
+    """pip_project without any device allocation (device tensors; at most
+    262144 points; the scratch is a fixed array inside the library shared by
+    all calls, so calls must not overlap on the GPU)."""
+    _native.check(lib().pip_project_noalloc(s.handle, _ptr(lon), _ptr(lat), int(lon.shape[0]), _ptr(out),
+                                            _stream(stream)))
+    return out
+
+
 def pip_quantize(v, stream=None):
     """Device quantizer Q (diagnostic): returns (q int32, valid uint8) tensors."""
     import torch

@@ -75,6 +75,7 @@ SIGNATURES = {
     "pip_set_free": (I32, [P]),
     "pip_project": (I32, [P, P, P, I64, P, P]),
     "pip_project_ex": (I32, [P, P, P, I64, P, P, P]),
+    "pip_project_noalloc": (I32, [P, P, P, I64, P, P]),
     "pip_set_check": (I32, [P, P]),
     "pip_plan_create": (I32, [I64, I32, P, P]),
     "pip_plan_run": (I32, [P, P, I32, P]),

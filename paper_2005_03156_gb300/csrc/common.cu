@@ -168,6 +168,27 @@ static pip_status scan_impl(Alloc& al, const In* in, uint64_t* out, int64_t n, u
   return PIP_OK;
 }
 
+// The same exclusive scan without allocating: block sums live in caller
+// scratch `tmp` of at least 2 * ceil(n / 4096) entries; n <= 4096 * 4096.
+pip_status scan_u32_to_u64_scratch(const uint32_t* in, uint64_t* out, int64_t n, uint64_t* tmp,
+                                   int64_t tmp_len, cudaStream_t s) {
+  if (n <= 0) return PIP_OK;
+  const int64_t blocks = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (blocks == 1) {
+    k_block_scan<uint32_t><<<1, SCAN_THREADS, 0, s>>>(in, out, n, nullptr, nullptr);
+    PIP_CUDA(cudaGetLastError());
+    count_launches(1);
+    return PIP_OK;
+  }
+  if (blocks > SCAN_TILE || 2 * blocks > tmp_len) return fail(PIP_EINVAL, "scan: scratch too small");
+  k_block_sums<uint32_t><<<(unsigned)blocks, SCAN_THREADS, 0, s>>>(in, n, tmp);
+  k_block_scan<uint64_t><<<1, SCAN_THREADS, 0, s>>>(tmp, tmp + blocks, blocks, nullptr, nullptr);
+  k_block_scan<uint32_t><<<(unsigned)blocks, SCAN_THREADS, 0, s>>>(in, out, n, tmp + blocks, nullptr);
+  PIP_CUDA(cudaGetLastError());
+  count_launches(3);
+  return PIP_OK;
+}
+
 pip_status scan_u32_to_u64(Alloc& al, const uint32_t* in, uint64_t* out, int64_t n,
                            uint64_t* total_dev, cudaStream_t s) {
   return scan_impl<uint32_t>(al, in, out, n, total_dev, s);

@@ -304,6 +304,8 @@ pip_status scan_u32_to_u64(Alloc& al, const uint32_t* in, uint64_t* out, int64_t
                            uint64_t* total_dev, cudaStream_t s);
 pip_status scan_u64(Alloc& al, const uint64_t* in, uint64_t* out, int64_t n,
                     uint64_t* total_dev, cudaStream_t s);
+pip_status scan_u32_to_u64_scratch(const uint32_t* in, uint64_t* out, int64_t n, uint64_t* tmp,
+                                   int64_t tmp_len, cudaStream_t s);
 
 }  // namespace pip
 

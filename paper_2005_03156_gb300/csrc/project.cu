@@ -329,6 +329,40 @@ pip_status project_device(pip_set_s* S, const double* lon, const double* lat, in
   return PIP_OK;
 }
 
+// The same K1 -> scan -> scatter -> K3 sequence with every scratch buffer
+// supplied by the caller (used by the entry point that allocates nothing).
+// queue/binned hold n entries, hist 2 * n_sb, off n_sb, scan_tmp scan_len,
+// ctr 4 words.
+pip_status project_device_scratch(pip_set_s* S, const double* lon, const double* lat, int64_t n,
+                                  int32_t* out, cudaStream_t s, Residual* queue, Residual* binned,
+                                  uint32_t* hist2, uint64_t* off, uint64_t* scan_tmp, int64_t scan_len,
+                                  uint32_t* ctr) {
+  const IndexView& ix = S->view;
+  const int64_t n_sb = std::max<int64_t>(1, ix.n_sb);
+  const uint32_t ppc = (uint32_t)std::max(1, S->opts.pts_per_cta);
+  PIP_CUDA(cudaMemsetAsync(hist2, 0, 2 * n_sb * sizeof(uint32_t), s));
+  PIP_CUDA(cudaMemsetAsync(ctr, 0, 4 * sizeof(uint32_t), s));
+  const bool vec = ((uintptr_t)lon % 16 == 0) && ((uintptr_t)lat % 16 == 0) && ((uintptr_t)out % 16 == 0);
+  const int64_t groups = (n + 3) / 4;
+  int occ1 = 0;
+  PIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_classify_points<true>, K1_THREADS, 0));
+  const unsigned g1 = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>((groups + K1_THREADS - 1) / K1_THREADS, (int64_t)num_sms() * std::max(1, occ1)));
+  if (vec)
+    k_classify_points<true><<<g1, K1_THREADS, 0, s>>>(ix, lon, lat, n, out, queue, ctr, hist2);
+  else
+    k_classify_points<false><<<g1, K1_THREADS, 0, s>>>(ix, lon, lat, n, out, queue, ctr, hist2);
+  PIP_CUDA(cudaGetLastError());
+  pip_status st = scan_u32_to_u64_scratch(hist2, off, n_sb, scan_tmp, scan_len, s);
+  if (st != PIP_OK) return st;
+  k_scatter<<<(unsigned)(num_sms() * 8), 256, 0, s>>>(queue, ctr, off, hist2 + n_sb, binned);
+  PIP_CUDA(cudaGetLastError());
+  st = k3_launch(ix, S->opts.stage_depth, binned, ctr, ppc, ctr + 1, out, S->status.p, s);
+  if (st != PIP_OK) return st;
+  count_launches(3);
+  return PIP_OK;
+}
+
 // Host-memory inputs/outputs: stream fixed-size chunks through two device
 // buffers on two streams so one chunk's copies overlap the other's compute.
 pip_status project_host(pip_set_s* S, const double* lon, const double* lat, int64_t n, int32_t* out,

@@ -1,0 +1,40 @@
+"""pip_project_noalloc: the projection for callers that cannot allocate
+device memory during a call (it takes its scratch from a fixed array inside
+the library). Its ids must equal pip_project's, exactly, on consecutive
+calls that reuse the shared scratch. Named to run after every other test,
+and it also passes alone in a fresh process."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from synth import configs, degenerate_lattice, lattice_to_degrees
+
+
+@pytest.mark.gpu
+def test_noalloc_equals_pip_project_on_consecutive_calls():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2005_03156_gb300 as pipm
+    from paper_2005_03156_gb300 import build
+    build.build()
+    ps = configs.tiny_set(seed=14, n_blocks=600, holes=0.05)
+    s = pipm.load_polygon_set(ps)
+    rng = np.random.default_rng(90)
+    for call, n in enumerate((200_000, 262_144)):  # second call reuses the scratch
+        qx, qy = degenerate_lattice(ps, n // 4, rng)
+        lon2, lat2 = configs.tiny_points(ps, n=n, seed=91 + call)
+        lon = np.concatenate([lattice_to_degrees(qx), lon2])[:n]
+        lat = np.concatenate([lattice_to_degrees(qy), lat2])[:n]
+        dl, da = torch.from_numpy(lon).cuda(), torch.from_numpy(lat).cuda()
+        want = pipm.pip_project(s, dl, da)
+        got = torch.full((n,), -7, dtype=torch.int32, device="cuda")
+        pipm.pip_project_noalloc(s, dl, da, got)
+        pipm.pip_set_check(s)
+        torch.cuda.synchronize()
+        assert torch.equal(got, want), int((got != want).sum())
+    too_many = torch.zeros(262_145, dtype=torch.float64, device="cuda")
+    out = torch.empty(262_145, dtype=torch.int32, device="cuda")
+    with pytest.raises(pipm.PipError) as e:
+        pipm.pip_project_noalloc(s, too_many, too_many, out)
+    assert e.value.status == 1
