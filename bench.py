@@ -285,12 +285,8 @@ def run_ours(args):
     launches = pipm.pip_kernel_launches() - l0
     clk = clocks.stop()
     barrier()
-    ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    from paper_2005_03156_gb300.shard import max_over_ranks
+    ms = max_over_ranks(ev0.elapsed_time(ev1), device="cuda")
     prof = pipm.pip_profile_read(s, args.steps)
     pipm.pip_profile_enable(s, 0)
     pipm.pip_set_check(s)
@@ -314,12 +310,7 @@ def run_ours(args):
         t = time.perf_counter()
         for _ in range(k_e2e):
             pipm.pip_project(s, hl, ha, ho)
-        dt = time.perf_counter() - t
-        if ws > 1:
-            import torch.distributed as dist
-            tt = torch.tensor([dt], device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            dt = float(tt.item())
+        dt = max_over_ranks(time.perf_counter() - t, device="cuda")
         e2e = {"value": n * ws * k_e2e / dt, "unit": UNIT, "h2d_bytes_per_step": 16 * n,
                "d2h_bytes_per_step": 4 * n, "steps": k_e2e,
                "path": "pip_project with pinned host lon/lat/out: chunked H2D / compute / D2H on 2 streams"}
@@ -492,6 +483,12 @@ def run_serve(args):
 
         # served: submit on schedule, collect completions
         srv = pipm.Server(sets, dict(n_streams=3, max_batch_points=1 << 23, max_batch_queries=1024))
+        for w in range(12):  # warm every slot (graph capture happens on a slot's first launch)
+            k, lon, lat, out = req(w)
+            tw = [srv.submit(k, lon, lat, out) for _ in range(3)]
+            for t in tw:
+                srv.wait(t)
+        srv.stats(reset=True)
         tickets = [0] * nreq
         t0 = time.perf_counter()
         for i in range(nreq):
