@@ -73,6 +73,12 @@ def _bind(lib):
     lib.orc_join_bruteforce.restype = None
     lib.orc_join_hier.argtypes = [P, P, P, P, I64, P, P, ctypes.c_int, P, P, I64, P, ctypes.c_int]
     lib.orc_join_hier.restype = None
+    lib.orc_hier_create.argtypes = [P, P, P, P, I64, P, P, ctypes.c_int]
+    lib.orc_hier_create.restype = P
+    lib.orc_hier_join.argtypes = [P, P, P, I64, P, ctypes.c_int]
+    lib.orc_hier_join.restype = None
+    lib.orc_hier_free.argtypes = [P]
+    lib.orc_hier_free.restype = None
     return lib
 
 
@@ -202,3 +208,28 @@ def join_hier(pset, lon, lat, threads: int | None = None, flat: bool = False, _u
     (_use or _load()).orc_join_hier(*args, _ptr(pf), _ptr(pl), nl, _ptr(lon), _ptr(lat), lon.size,
                           _ptr(out), threads or default_threads())
     return out
+
+
+class Hier:
+    """O1 with its box hierarchy prepared once (for repeated joins against
+    the same set, e.g. the timed CPU baseline)."""
+
+    def __init__(self, pset, threads: int | None = None):
+        self._keep, args = _poly_args(pset)
+        self._pf, self._pl, nl = _parents_flat(pset)
+        self._lib = _load()
+        self.threads = threads or default_threads()
+        self.h = self._lib.orc_hier_create(*args, _ptr(self._pf), _ptr(self._pl), nl)
+
+    def join(self, lon, lat, threads: int | None = None) -> np.ndarray:
+        lon = _c(lon, np.float64)
+        lat = _c(lat, np.float64)
+        out = np.zeros(lon.shape, np.int32)
+        self._lib.orc_hier_join(self.h, _ptr(lon), _ptr(lat), lon.size, _ptr(out),
+                                threads or self.threads)
+        return out
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self._lib.orc_hier_free(self.h)
+            self.h = None

@@ -307,6 +307,40 @@ void orc_join_bruteforce(const int32_t* vx, const int32_t* vy, const int64_t* ri
   });
 }
 
+// O1 with the hierarchy prepared once and reused across calls (a handle owns
+// the boxes and child lists; the polygon arrays stay the caller's).
+struct HierHandle {
+  PolySet s;
+  Hierarchy h;
+};
+
+void* orc_hier_create(const int32_t* vx, const int32_t* vy, const int64_t* ring_off,
+                      const int64_t* poly_ring_off, int64_t n_poly, const int32_t* parent_flat,
+                      const int64_t* level_len, int n_levels) {
+  HierHandle* H = new HierHandle{PolySet{vx, vy, ring_off, poly_ring_off, n_poly}, Hierarchy{}};
+  H->h = build_hierarchy(H->s, parent_flat, level_len, n_levels);
+  return H;
+}
+
+void orc_hier_join(void* handle, const double* x_pt, const double* y_pt, int64_t n, int32_t* out,
+                   int n_threads) {
+  const HierHandle* H = (const HierHandle*)handle;
+  parallel_for(n, n_threads, [&](int64_t a, int64_t b) {
+    std::vector<int64_t> cand;
+    std::vector<std::pair<int, int64_t>> stack;
+    for (int64_t i = a; i < b; ++i) {
+      int32_t px, py;
+      if (!quantize(x_pt[i], &px) || !quantize(y_pt[i], &py)) {
+        out[i] = -1;
+        continue;
+      }
+      out[i] = hierarchical_one(H->s, H->h, px, py, cand, stack);
+    }
+  });
+}
+
+void orc_hier_free(void* handle) { delete (HierHandle*)handle; }
+
 // O1 on double coordinates. parent_flat holds the parent arrays of levels
 // 0..n_levels-1 back to back; level_len[l] is the length of level l's array
 // (level_len[0] = n_poly). n_levels = 0 means a flat set.
