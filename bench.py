@@ -532,6 +532,11 @@ def run_serve(args):
     print(json.dumps(line))
 
 
+def _national_chunk(a):
+    from synth import configs
+    return configs.national_points_chunk(*a)
+
+
 def run_national(args):
     """1e9 mixture points over 50 regions (800,000 blocks) streamed from
     pinned host memory in 1e8-point chunks through pip_project."""
@@ -552,10 +557,12 @@ def run_national(args):
     lon_h = torch.empty(n_chunks * chunk, dtype=torch.float64).pin_memory()
     lat_h = torch.empty(n_chunks * chunk, dtype=torch.float64).pin_memory()
     out_h = torch.empty(n_chunks * chunk, dtype=torch.int32).pin_memory()
-    for c in range(n_chunks):
-        lon, lat = npts.chunk(c, chunk)
-        lon_h[c * chunk:(c + 1) * chunk] = torch.from_numpy(lon)
-        lat_h[c * chunk:(c + 1) * chunk] = torch.from_numpy(lat)
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(min(n_chunks, max(1, (os.cpu_count() or 2) // 2))) as pool:
+        for c, (lon, lat) in enumerate(pool.imap(_national_chunk, [(c, chunk) for c in range(n_chunks)])):
+            lon_h[c * chunk:(c + 1) * chunk] = torch.from_numpy(lon)
+            lat_h[c * chunk:(c + 1) * chunk] = torch.from_numpy(lat)
+    del npts
     gen_pts = time.perf_counter() - t0 - gen_set
     # pinned H2D bandwidth probe
     dbuf = torch.empty(chunk, dtype=torch.float64, device="cuda")

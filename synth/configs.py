@@ -99,23 +99,34 @@ def state_points(n=100_000_000, seed=SEEDS["state"], box_deg=STATE_BOX_DEG, stre
 
 
 def national_regions(seed=SEEDS["national"], n_regions=50):
-    """50 disjoint boxes of 3-10 degrees inside lon [-125,-65] x lat [24,50]."""
+    """50 disjoint boxes with sides in 3-10 degrees inside lon [-125,-65] x
+    lat [24,50]: sides drawn skewed towards 3 degrees (the window holds only
+    ~1,560 square degrees); a box that cannot be placed shrinks (not below
+    3 degrees) until it fits."""
     rng = _rng(seed, 20)
     boxes = []
-    tries = 0
+
+    def free(b):
+        return all(b[2] <= c[0] or c[2] <= b[0] or b[3] <= c[1] or c[3] <= b[1] for c in boxes)
+
     while len(boxes) < n_regions:
-        tries += 1
-        w = rng.uniform(3, 10)
-        h = rng.uniform(3, 10)
-        x0 = rng.uniform(-125, -65 - w)
-        y0 = rng.uniform(24, 50 - h)
-        b = (x0, y0, x0 + w, y0 + h)
-        if all(b[2] <= c[0] or c[2] <= b[0] or b[3] <= c[1] or c[3] <= b[1] for c in boxes):
-            boxes.append(b)
-        if tries > 200000:
-            # shrink sizes if the plane gets crowded
-            boxes = []
-            tries = 0
+        w = 3.0 + 7.0 * rng.random() ** 3
+        h = 3.0 + 7.0 * rng.random() ** 3
+        placed = False
+        while not placed:
+            for _ in range(400):
+                x0 = rng.uniform(-125, -65 - w)
+                y0 = rng.uniform(24, 50 - h)
+                b = (x0, y0, x0 + w, y0 + h)
+                if free(b):
+                    boxes.append(b)
+                    placed = True
+                    break
+            if not placed:
+                if w <= 3.0 and h <= 3.0:
+                    boxes = []  # start over with the rng's next values
+                    break
+                w, h = max(3.0, 0.9 * w), max(3.0, 0.9 * h)
     return [tuple(round(v, 4) for v in b) for b in boxes]
 
 
@@ -155,15 +166,27 @@ class NationalPoints:
         self.seed = seed
 
     def chunk(self, i, n):
+        """Chunk i of n points: an i.i.d. region label per point; each
+        region's points are drawn i.i.d. from its mixture and placed at that
+        region's positions (so the stream is in random spatial order)."""
         rng = _rng(self.seed, 5000 + i)
-        reg = rng.choice(len(self.mixes), n, p=self.p)
+        cdf = np.cumsum(self.p)
+        cdf[-1] = 1.0
+        reg = np.minimum(np.searchsorted(cdf, rng.random(n), side="right"),
+                         len(self.mixes) - 1).astype(np.uint8)
+        order = np.argsort(reg, kind="stable")
+        counts = np.bincount(reg, minlength=len(self.mixes))
         lon = np.empty(n, np.float64)
         lat = np.empty(n, np.float64)
-        for r in np.unique(reg):
-            m = reg == r
-            pts = self.mixes[r].sample_units(int(m.sum()), rng)
-            lon[m] = pts[:, 0] / UNITS_PER_DEG
-            lat[m] = pts[:, 1] / UNITS_PER_DEG
+        at = 0
+        for r, c in enumerate(counts):
+            if not c:
+                continue
+            pts = self.mixes[r].sample_units_iid(int(c), rng)
+            pos = order[at:at + c]
+            lon[pos] = pts[:, 0] / UNITS_PER_DEG
+            lat[pos] = pts[:, 1] / UNITS_PER_DEG
+            at += c
         return lon, lat
 
 
@@ -206,3 +229,9 @@ def batched_query_sizes(seed=SEEDS["batched"], n_queries=4096, lo=100, hi=1_000_
     s = np.exp(np.log(median) + sig * rng.standard_normal(n_queries * 4))
     s = s[(s >= lo) & (s <= hi)][:n_queries]
     return np.rint(s).astype(np.int64), sig
+
+
+def national_points_chunk(i, n, seed=SEEDS["national"]):
+    """Chunk i (lon, lat) of the national point stream (picklable helper for
+    process pools)."""
+    return NationalPoints(seed).chunk(i, n)

@@ -104,6 +104,23 @@ class Mixture:
             pts = pts[:n]
         return pts[rng.permutation(len(pts))]
 
+    def sample_units_iid(self, n, rng):
+        """n points in lattice units, each independently from the mixture
+        (component 64 = the uniform share), so their order needs no shuffle."""
+        X0, Y0, X1, Y1 = self.box
+        k = len(self.weights)
+        p = np.concatenate([self.weights * (1.0 - self.uniform_frac), [self.uniform_frac]])
+        cdf = np.cumsum(p)
+        cdf[-1] = 1.0
+        comp = np.minimum(np.searchsorted(cdf, rng.random(n), side="right"), k)
+        sig = np.concatenate([self.sigma, [0.0]])[comp]
+        cx = np.concatenate([self.centres[:, 0], [0.0]])[comp]
+        cy = np.concatenate([self.centres[:, 1], [0.0]])[comp]
+        uni = comp == k
+        x = np.where(uni, rng.uniform(X0, X1, n), rng.standard_normal(n) * sig + cx)
+        y = np.where(uni, rng.uniform(Y0, Y1, n), rng.standard_normal(n) * sig + cy)
+        return np.c_[x, y]
+
     def sample_degrees(self, n, rng, chunk=1 << 24):
         """n points as float64 lon/lat degrees, generated in chunks."""
         lon = np.empty(n, np.float64)
