@@ -372,7 +372,7 @@ def run_batched(args):
     set_of = rng.integers(0, len(psets), len(sizes))
     sets = [pipm.load_polygon_set(p) for p in psets]
     # points: each set's mixture, one block of points per set, queries slice it
-    per_set = [int(sizes[set_of == k].sum()) for k in range(len(psets))]
+    per_set = [int(sizes[set_of == k].sum()) + 2 * int((set_of == k).sum()) for k in range(len(psets))]
     pts = []
     for k, p in enumerate(psets):
         lon, lat = p.meta["mixture"].sample_degrees(max(1, per_set[k]),
@@ -390,6 +390,7 @@ def run_batched(args):
         k = int(set_of[i])
         a = used[k]
         used[k] += int(n)
+        used[k] = min(per_set[k], (used[k] + 1) // 2 * 2)  # queries start 16-byte aligned
         out = torch.empty(int(n), dtype=torch.int32, device="cuda")
         qs.append((sets[k], pts[k][0][a:a + n], pts[k][1][a:a + n], out))
         outs.append(out)

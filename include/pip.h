@@ -196,6 +196,14 @@ pip_status pip_project_ex(pip_set set, const double* lon, const double* lat, int
 pip_status pip_project_noalloc(pip_set set, const double* lon, const double* lat, int64_t n,
                                int32_t* out, void* stream);
 
+/* Hierarchical outputs (Appendix A assigns state and county codes before the
+ * block code): out[i] = the level-`level` ancestor of block id ids[i] through
+ * the parent arrays given at load (0 = the block itself, 1 = its tract,
+ * 2 = county, 3 = region ...); -1 stays -1. Device pointers, asynchronous.
+ * PIP_EINVAL if level exceeds the set's levels. */
+pip_status pip_parent_ids(pip_set set, const int32_t* ids, int64_t n, int32_t level, int32_t* out,
+                          void* stream);
+
 /* Device error word of the set (a bounded device wait that ran out sets it):
  * synchronises `stream`, returns PIP_OK or PIP_ETIMEOUT and clears it. */
 pip_status pip_set_check(pip_set set, void* stream);

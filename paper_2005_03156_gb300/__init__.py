@@ -177,6 +177,15 @@ def pip_project_noalloc(s: PolygonSet, lon, lat, out, stream=None):
     return out
 
 
+def pip_parent_ids(s: PolygonSet, ids, level: int, stream=None):
+    """Level-`level` ancestors of block ids (1 = tract, 2 = county, ...)."""
+    import torch
+    out = torch.empty_like(ids)
+    _native.check(lib().pip_parent_ids(s.handle, _ptr(ids), int(ids.shape[0]), int(level), _ptr(out),
+                                       _stream(stream)))
+    return out
+
+
 def pip_quantize(v, stream=None):
     """Device quantizer Q (diagnostic): returns (q int32, valid uint8) tensors."""
     import torch

@@ -77,6 +77,7 @@ SIGNATURES = {
     "pip_project_ex": (I32, [P, P, P, I64, P, P, P]),
     "pip_project_noalloc": (I32, [P, P, P, I64, P, P]),
     "pip_set_check": (I32, [P, P]),
+    "pip_parent_ids": (I32, [P, P, I64, I32, P, P]),
     "pip_plan_create": (I32, [I64, I32, P, P]),
     "pip_plan_run": (I32, [P, P, I32, P]),
     "pip_plan_check": (I32, [P, P]),

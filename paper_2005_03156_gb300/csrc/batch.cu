@@ -180,21 +180,39 @@ __global__ void __launch_bounds__(B_THREADS) k_batch(PlanBufs B) {
     const DevQuery q = B.queries[tl.x];
     const DevSet& S = s_sets[q.set];
     const uint32_t slot_add = S.sb_base << SB_LOG2;
+    const double* lon = q.lon + tl.y;
+    const double* lat = q.lat + tl.y;
+    int32_t* out = q.out + tl.y;
+    // 16-byte loads / stores when the tile's three arrays are aligned
+    const bool vec = (((uintptr_t)lon | (uintptr_t)lat | (uintptr_t)out) & 15u) == 0;
     for (uint32_t g0 = 0; g0 < tl.z; g0 += 4 * blockDim.x) {
       const uint32_t j0 = g0 + 4 * threadIdx.x;  // offset within the tile
       double x[4], y[4];
+      if (vec && j0 + 3 < tl.z) {
+        const double2 a0 = __ldcs(reinterpret_cast<const double2*>(lon + j0));
+        const double2 a1 = __ldcs(reinterpret_cast<const double2*>(lon + j0) + 1);
+        const double2 b0 = __ldcs(reinterpret_cast<const double2*>(lat + j0));
+        const double2 b1 = __ldcs(reinterpret_cast<const double2*>(lat + j0) + 1);
+        x[0] = a0.x; x[1] = a0.y; x[2] = a1.x; x[3] = a1.y;
+        y[0] = b0.x; y[1] = b0.y; y[2] = b1.x; y[3] = b1.y;
+      } else {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const bool have = j0 + j < tl.z;
-        x[j] = have ? __ldcs(q.lon + tl.y + j0 + j) : __longlong_as_double(0x7FF8000000000000ll);
-        y[j] = have ? __ldcs(q.lat + tl.y + j0 + j) : 0.0;
+        for (int j = 0; j < 4; ++j) {
+          const bool have = j0 + j < tl.z;
+          x[j] = have ? __ldcs(lon + j0 + j) : __longlong_as_double(0x7FF8000000000000ll);
+          y[j] = have ? __ldcs(lat + j0 + j) : 0.0;
+        }
       }
       int32_t id[4], qx[4], qy[4];
       uint32_t d[4];
       const uint32_t mask = classify4(S.view, x, y, id, qx, qy, d);
+      if (vec && j0 + 3 < tl.z) {
+        __stcs(reinterpret_cast<int4*>(out + j0), make_int4(id[0], id[1], id[2], id[3]));
+      } else {
 #pragma unroll
-      for (int j = 0; j < 4; ++j)
-        if (j0 + j < tl.z) q.out[tl.y + j0 + j] = id[j];
+        for (int j = 0; j < 4; ++j)
+          if (j0 + j < tl.z) out[j0 + j] = id[j];
+      }
       append_residual(mask, qx, qy, d, tl.w + j0, B.queue, B.ctr + 0, B.hist, slot_add);
     }
   }

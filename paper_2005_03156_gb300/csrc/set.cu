@@ -213,3 +213,39 @@ extern "C" pip_status pip_profile_read(pip_set set, double* k1_ms, double* bin_m
   set->prof_n = 0;
   return PIP_OK;
 }
+
+namespace pip {
+struct ParentChain {
+  const int32_t* level[MAX_LEVELS];
+  int32_t n_levels;
+};
+
+// out[i] = the level-`level` ancestor of block ids[i] (-1 stays -1).
+__global__ void k_parent_ids(ParentChain pc, const int32_t* __restrict__ ids, int64_t n,
+                             int32_t* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t v = ids[i];
+    for (int l = 0; l < pc.n_levels && v >= 0; ++l) v = pc.level[l][v];
+    out[i] = v;
+  }
+}
+}  // namespace pip
+
+extern "C" pip_status pip_parent_ids(pip_set set, const int32_t* ids, int64_t n, int32_t level,
+                                     int32_t* out, void* stream) {
+  if (!set) return fail(PIP_EINVAL, "pip_parent_ids: NULL set");
+  if (n < 0 || level < 0 || level > (int32_t)set->parent.size())
+    return fail(PIP_EINVAL, "pip_parent_ids: bad n or level");
+  if (n == 0) return PIP_OK;
+  if (!ids || !out || !is_device_ptr(ids) || !is_device_ptr(out))
+    return fail(PIP_EINVAL, "pip_parent_ids: ids and out must be device memory");
+  ParentChain pc{};
+  pc.n_levels = level;
+  for (int l = 0; l < level; ++l) pc.level[l] = set->parent[l].p;
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, num_sms() * 8));
+  k_parent_ids<<<g, 256, 0, (cudaStream_t)stream>>>(pc, ids, n, out);
+  PIP_CUDA(cudaGetLastError());
+  count_launches(1);
+  return PIP_OK;
+}

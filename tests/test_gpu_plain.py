@@ -266,3 +266,16 @@ def test_axis_aligned_partition(pipm, opts):
     assert (got == want).all(), int((got != want).sum())
     inside = (qx >= box[0]) & (qx < box[2]) & (qy >= box[1]) & (qy < box[3])
     assert (got[inside] >= 0).all() and (got[~inside] == -1).all()
+
+
+def test_parent_ids_follow_the_hierarchy(pipm, tiny_set):
+    s = pipm.load_polygon_set(tiny_set)
+    lon, lat = configs.tiny_points(tiny_set, n=50_000, seed=55)
+    ids = pipm.pip_project(s, dev(lon), dev(lat))
+    want = ids.cpu().numpy()
+    for level, par in enumerate(tiny_set.parents, start=1):
+        got = pipm.pip_parent_ids(s, ids, level).cpu().numpy()
+        want = np.where(want >= 0, par[np.maximum(want, 0)], -1)
+        assert (got == want).all(), level
+    with pytest.raises(pipm.PipError):
+        pipm.pip_parent_ids(s, ids, len(tiny_set.parents) + 1)
