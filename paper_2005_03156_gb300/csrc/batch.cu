@@ -28,6 +28,7 @@ namespace pip {
 
 constexpr int B_THREADS = 256;
 constexpr int TILE = 4096;
+static_assert(TILE == 4096, "tile offsets use 12 bits");
 constexpr int MAX_SETS = 64;
 
 struct DevSet {
@@ -91,18 +92,16 @@ __device__ __forceinline__ void grid_barrier(const PlanBufs& B, uint32_t nblocks
   __syncthreads();
 }
 
+// Residual entries of the batched form carry z = tile << 12 | offset in the
+// tile (tiles never cross queries), so the output slot is two cached loads.
+constexpr int TILE_LOG2 = 12;
+
 struct BatchStore {
-  const uint32_t* qoff;
+  const uint4* tiles;
   const DevQuery* queries;
-  uint32_t n_q;
   __device__ __forceinline__ void operator()(const Residual& r, int32_t id) const {
-    // query holding global point r.z: last q with qoff[q] <= r.z
-    uint32_t lo = 0, hi = n_q;
-    while (hi - lo > 1) {
-      const uint32_t mid = (lo + hi) >> 1;
-      if (qoff[mid] <= r.z) lo = mid; else hi = mid;
-    }
-    queries[lo].out[r.z - qoff[lo]] = id;
+    const uint4 tl = tiles[r.z >> TILE_LOG2];
+    queries[tl.x].out[tl.y + (r.z & (TILE - 1))] = id;
   }
 };
 
@@ -213,7 +212,7 @@ __global__ void __launch_bounds__(B_THREADS) k_batch(PlanBufs B) {
         for (int j = 0; j < 4; ++j)
           if (j0 + j < tl.z) out[j0 + j] = id[j];
       }
-      append_residual(mask, qx, qy, d, tl.w + j0, B.queue, B.ctr + 0, B.hist, slot_add);
+      append_residual(mask, qx, qy, d, (w << TILE_LOG2) + j0, B.queue, B.ctr + 0, B.hist, slot_add);
     }
   }
   grid_barrier(B, nblocks);
@@ -282,7 +281,7 @@ __global__ void __launch_bounds__(B_THREADS) k_batch(PlanBufs B) {
   // ---- phase 3: crossing tests, chunks of ppc binned points
   const uint32_t ppc = H.ppc;
   const uint32_t n_items = (n_res + ppc - 1) / ppc;
-  const BatchStore store{B.qoff, B.queries, H.n_q};
+  const BatchStore store{B.tiles, B.queries};
   uint32_t phase = 0;
   while (true) {
     if (threadIdx.x == 0) {
@@ -336,7 +335,7 @@ struct pip_plan_s {
   int grid = 0;
   int staged = 0;      // 0 unstaged, 1 staged
   uint32_t ppc = 256;
-  uint32_t stage_bytes = 48 * 1024;
+  uint32_t stage_bytes = 16 * 1024;  // small: the one kernel's other phases want L1
   Alloc alloc;
   DBuf<uint8_t> tables;  // header | sets | queries | qoff | tiles
   size_t tables_bytes = 0;
@@ -451,6 +450,8 @@ extern "C" pip_status pip_plan_create(int64_t max_points, int32_t max_queries, v
   P->max_points = max_points;
   P->max_queries = max_queries;
   P->max_tiles = max_points / TILE + max_queries + 1;
+  if (P->max_tiles >= (1ll << (32 - TILE_LOG2)))
+    return fail(PIP_EINVAL, "pip_plan_create: too many tiles (max_points / 4096 + max_queries < 2^20)");
   P->off_sets = align_up(sizeof(RunHeader), 256);
   P->off_q = align_up(P->off_sets + sizeof(DevSet) * MAX_SETS, 256);
   P->off_qoff = align_up(P->off_q + sizeof(DevQuery) * (size_t)max_queries, 256);
