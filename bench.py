@@ -332,7 +332,7 @@ def run_ours(args):
                                                       "interior_cells", "superbins", "index_bytes",
                                                       "build_ms", "table_entries")},
                        "residual_fraction": pstats["residual"] / n},
-            "roofline": {"bound": "hbm", "kernel": "k_classify_points (K1)", "achieved": achieved,
+            "roofline": {"bound": "hbm", "kernel": "k_classify_dq (K1)", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json copy bandwidth)",
                          "bytes_per_launch": BYTES_PER_POINT * n},

@@ -167,7 +167,9 @@ pip_status pip_set_free(pip_set set);
  * lon, lat and out are device pointers. With host pointers the call streams
  * the points through the device in chunks (pinned host memory overlaps the
  * copies with compute) and returns after out[] is written.
- * out must not alias lon or lat. n < 2^32 per call when device-resident. */
+ * out must not alias lon or lat. When device-resident, n must stay about
+ * 1M below 2^32 per call (the residual queue is indexed with 32 bits and
+ * holds n plus two reserved chunks per warp); larger n gives PIP_EINVAL. */
 pip_status pip_project(pip_set set, const double* lon, const double* lat, int64_t n,
                        int32_t* out, void* stream);
 

@@ -74,12 +74,14 @@ __device__ __forceinline__ void lookup4(const IndexView& ix, const int32_t (&qx)
 }
 
 // Append up to 4 residual points of this lane to the queue with one atomic
-// per warp; count them per superbin (hist may be offset per set).
-__device__ __forceinline__ void append_residual(uint32_t mask, const int32_t (&qx)[4],
-                                                const int32_t (&qy)[4], const uint32_t (&d)[4],
-                                                uint32_t idx0, Residual* __restrict__ queue,
-                                                uint32_t* __restrict__ qcount,
-                                                uint32_t* __restrict__ hist, uint32_t slot_add) {
+// per warp; count them per superbin (hist may be offset per set). idx_of(j)
+// is the index of slot j's point.
+template <class IdxOf>
+__device__ __forceinline__ void append_residual_at(uint32_t mask, const int32_t (&qx)[4],
+                                                   const int32_t (&qy)[4], const uint32_t (&d)[4],
+                                                   IdxOf idx_of, Residual* __restrict__ queue,
+                                                   uint32_t* __restrict__ qcount,
+                                                   uint32_t* __restrict__ hist, uint32_t slot_add) {
   const uint32_t full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   if (!__any_sync(full, mask != 0u)) return;
@@ -97,10 +99,20 @@ __device__ __forceinline__ void append_residual(uint32_t mask, const int32_t (&q
   for (int j = 0; j < 4; ++j) {
     if (mask & (1u << j)) {
       const uint32_t slot = (d[j] & PAYLOAD_MASK) + slot_add;
-      queue[base++] = make_uint4((uint32_t)qx[j], (uint32_t)qy[j], idx0 + j, slot);
+      queue[base++] = make_uint4((uint32_t)qx[j], (uint32_t)qy[j], idx_of(j), slot);
       atomicAdd(hist + (slot >> SB_LOG2), 1u);
     }
   }
+}
+
+// Slot j holds point idx0 + j.
+__device__ __forceinline__ void append_residual(uint32_t mask, const int32_t (&qx)[4],
+                                                const int32_t (&qy)[4], const uint32_t (&d)[4],
+                                                uint32_t idx0, Residual* __restrict__ queue,
+                                                uint32_t* __restrict__ qcount,
+                                                uint32_t* __restrict__ hist, uint32_t slot_add) {
+  append_residual_at(mask, qx, qy, d, [idx0](int j) { return idx0 + (uint32_t)j; }, queue, qcount,
+                     hist, slot_add);
 }
 
 // Classify 4 points; returns their ids (-1 for residual ones) and the

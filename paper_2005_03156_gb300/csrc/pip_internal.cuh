@@ -127,6 +127,8 @@ __device__ __forceinline__ uint32_t node_step(const NodeWords& n, uint32_t sub) 
 // x = qx, y = qy, z = index of the point within the call (or batch),
 // w = leaf slot (superbin = slot >> 5).
 typedef uint4 Residual;
+// w of a queue entry that was reserved but never written (skipped by K2)
+constexpr uint32_t RES_HOLE = 0xFFFFFFFFu;
 
 // ---------------------------------------------------------------------------
 // Q(v) on the device with integer instructions only (GB300's double rate is

@@ -72,6 +72,219 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_classify_points(
   }
 }
 
+// ------------------------------------------------------ K1, deferred-queue form
+// In the lockstep form above a lane walks its 4 points level by level, so at
+// every level the warp waits for the deepest of its 128 points (in the state
+// workload ~39 % of points stop at the top grid, ~38 % one level down, ~20 %
+// two, ~3 % three, yet nearly every warp takes all three node levels). Here
+// a step of 4 points per lane only quantizes them and reads their top-grid
+// descriptors; points whose cell is split go onto a per-warp ring in shared
+// memory, and whenever the ring holds 128 entries the warp takes one trie
+// level for all of them at once (4 per lane) and puts back the ones that
+// are still split. Every dependent index load then serves a live point, and
+// the lanes stay converged. Ids of points resolved below the top grid are
+// stored one by one; their sectors were written by the step's 16-byte store
+// moments before and are still in L2. Residual points go straight to the
+// global queue into a chunk of DQ_CHUNK entries the warp reserved earlier;
+// the atomic that reserves the following chunk is issued as soon as the
+// current one is taken, so no trie level waits on it. Entries a warp
+// reserved but did not fill are marked RES_HOLE (K2 skips them); the real
+// residual count goes to qcount[2] once per warp at the end. (Atomics on one
+// shared address are serialised in L2: one per trie level per warp cost as
+// much as the whole walk.)
+// Shared memory holds only the ring (17 KB a CTA): the rest of the SM's
+// 256 KB stays L1, which holds the sectors of the index loads in flight; a
+// larger carve-out measurably throttles them.
+constexpr int DQ_RING = 256;    // ring entries per warp (at most 255 are ever held)
+constexpr int DQ_THREADS = 128;
+constexpr uint32_t DQ_CHUNK = 256;  // >= 128, the most one step can queue
+
+template <bool VEC>
+__global__ void __launch_bounds__(DQ_THREADS, 6) k_classify_dq(
+    IndexView ix, const double* __restrict__ lon, const double* __restrict__ lat, int64_t n,
+    int32_t* __restrict__ out, Residual* __restrict__ queue, uint32_t* __restrict__ qcount,
+    uint32_t* __restrict__ hist) {
+  __shared__ uint4 ring[DQ_THREADS / 32][DQ_RING];      // (qx, qy, point, node)
+  __shared__ uint8_t ring_sh[DQ_THREADS / 32][DQ_RING];  // shift of the node's children
+  const uint32_t full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  uint4* rq = ring[threadIdx.x >> 5];
+  uint8_t* rs = ring_sh[threadIdx.x >> 5];
+  uint32_t head = 0, count = 0;  // warp-uniform
+  const uint64_t pol = policy_evict_last();
+  const uint32_t m = (1u << NODE_K) - 1u;
+
+  // residual chunks: the current one [cb, cb + DQ_CHUNK) has cu entries used;
+  // lane 0 holds the base of the next one, reserved in advance
+  uint32_t nb = 0;
+  if (lane == 0) nb = atomicAdd(qcount, DQ_CHUNK);
+  uint32_t cb = __shfl_sync(full, nb, 0), cu = 0;
+  if (lane == 0) nb = atomicAdd(qcount, DQ_CHUNK);
+  uint32_t wreal = 0;  // residual points this warp queued
+
+  // append the slots in mask (boundary leaves) to the queue
+  auto put_leaves = [&](uint32_t mask, const int32_t(&qx)[4], const int32_t(&qy)[4],
+                        const uint32_t(&idx)[4], const uint32_t(&d)[4]) {
+    const uint32_t c = __popc(mask);
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(full, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const uint32_t tot = __shfl_sync(full, incl, 31);
+    const uint32_t nbb = __shfl_sync(full, nb, 0);  // waits only if the reservation is still in flight
+    uint32_t r = cu + incl - c;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if ((mask >> j) & 1u) {
+        const uint32_t slot = d[j] & PAYLOAD_MASK;
+        const uint32_t at = r < DQ_CHUNK ? cb + r : nbb + (r - DQ_CHUNK);
+        queue[at] = make_uint4((uint32_t)qx[j], (uint32_t)qy[j], idx[j], slot);
+        atomicAdd(hist + (slot >> SB_LOG2), 1u);
+        ++r;
+      }
+    }
+    cu += tot;
+    if (cu >= DQ_CHUNK) {  // the next chunk becomes current; reserve another
+      cb = nbb;
+      cu -= DQ_CHUNK;
+      if (lane == 0) nb = atomicAdd(qcount, DQ_CHUNK);
+    }
+    wreal += tot;
+  };
+
+  // append the slots in mask (split cells: node d, child shift sh) to the ring
+  auto push = [&](uint32_t mask, const int32_t(&qx)[4], const int32_t(&qy)[4], const uint32_t(&idx)[4],
+                  const uint32_t(&d)[4], const int(&sh)[4]) {
+    const uint32_t c = __popc(mask);
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(full, incl, o);
+      if (lane >= o) incl += t;
+    }
+    uint32_t pos = head + count + incl - c;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if ((mask >> j) & 1u) {
+        const uint32_t p = pos++ & (DQ_RING - 1);
+        rq[p] = make_uint4((uint32_t)qx[j], (uint32_t)qy[j], idx[j], d[j] & PAYLOAD_MASK);
+        rs[p] = (uint8_t)sh[j];
+      }
+    }
+    count += __shfl_sync(full, incl, 31);
+  };
+
+  // one trie level for the ring's first `take` entries (take <= 128, uniform)
+  auto step_ring = [&](uint32_t take) {
+    __syncwarp();
+    int32_t qx[4], qy[4];
+    uint32_t idx[4], d[4];
+    int sh[4];
+    uint32_t have = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t k = (uint32_t)lane + 32u * j;
+      qx[j] = qy[j] = 0;
+      idx[j] = d[j] = 0u;
+      sh[j] = 0;
+      if (k < take) {
+        const uint32_t p = (head + k) & (DQ_RING - 1);
+        const uint4 e = rq[p];
+        qx[j] = (int32_t)e.x;
+        qy[j] = (int32_t)e.y;
+        idx[j] = e.z;
+        d[j] = e.w;
+        sh[j] = rs[p];
+        have |= 1u << j;
+      }
+    }
+    head += take;
+    count -= take;
+    __syncwarp();  // every entry is read before the pushes below reuse slots
+    NodeWords nw[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if ((have >> j) & 1u) nw[j] = ld_node(ix.nodes, d[j], pol);
+    uint32_t leaf = 0, again = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if ((have >> j) & 1u) {
+        const uint32_t dx = (uint32_t)qx[j] - (uint32_t)ix.gx0, dy = (uint32_t)qy[j] - (uint32_t)ix.gy0;
+        const uint32_t sub = (((dy >> sh[j]) & m) << NODE_K) | ((dx >> sh[j]) & m);
+        d[j] = node_step(nw[j], sub);
+        const uint32_t tag = d[j] >> 30;
+        if (tag == TAG_INTERIOR) out[idx[j]] = (int32_t)(d[j] & PAYLOAD_MASK);
+        leaf |= (tag == TAG_LEAF ? 1u : 0u) << j;
+        again |= (tag == TAG_CHILD ? 1u : 0u) << j;
+        sh[j] -= NODE_K;
+      }
+    }
+    if (__any_sync(full, leaf != 0u)) put_leaves(leaf, qx, qy, idx, d);
+    if (__any_sync(full, again != 0u)) push(again, qx, qy, idx, d, sh);
+  };
+
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t groups = (n + 3) / 4;
+  const int64_t rounds = (groups + stride - 1) / stride;  // whole warps iterate together
+  double nx[4], ny[4];
+  load4<VEC>(lon, lat, n, tid, nx, ny);
+#pragma unroll 1
+  for (int64_t it = 0; it < rounds; ++it) {
+    const int64_t g = it * stride + tid;
+    const int64_t i0 = g * 4;
+    double x[4], y[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      x[j] = nx[j];
+      y[j] = ny[j];
+    }
+    if (it + 1 < rounds) load4<VEC>(lon, lat, n, g + stride, nx, ny);
+    int32_t qx[4], qy[4], id[4];
+    uint32_t d[4], idx[4];
+    int sh[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      qx[j] = qy[j] = 0;
+      const bool ok = quantize_double(x[j], qx[j]) & quantize_double(y[j], qy[j]);
+      const uint32_t dx = (uint32_t)qx[j] - (uint32_t)ix.gx0, dy = (uint32_t)qy[j] - (uint32_t)ix.gy0;
+      const uint32_t cx = dx >> ix.s0, cy = dy >> ix.s0;
+      const bool in = ok & (cx < ix.nx) & (cy < ix.ny) & (qx[j] >= ix.gx0) & (qy[j] >= ix.gy0);
+      d[j] = in ? ld_index_u32(ix.table + (size_t)cy * ix.nx + cx, pol) : 0u;
+      idx[j] = (uint32_t)i0 + j;
+      sh[j] = ix.s0 - NODE_K;
+    }
+    uint32_t leaf = 0, split = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t tag = d[j] >> 30;
+      id[j] = tag == TAG_INTERIOR ? (int32_t)(d[j] & PAYLOAD_MASK) : -1;
+      leaf |= (tag == TAG_LEAF ? 1u : 0u) << j;
+      split |= (tag == TAG_CHILD ? 1u : 0u) << j;
+    }
+    if (VEC && i0 + 3 < n) {
+      reinterpret_cast<int4*>(out)[g] = make_int4(id[0], id[1], id[2], id[3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (i0 + j < n) out[i0 + j] = id[j];
+    }
+    if (__any_sync(full, leaf != 0u)) put_leaves(leaf, qx, qy, idx, d);
+    if (__any_sync(full, split != 0u)) push(split, qx, qy, idx, d, sh);
+#pragma unroll 1
+    while (count >= 128u) step_ring(128u);
+  }
+#pragma unroll 1
+  while (count > 0u) step_ring(count < 128u ? count : 128u);
+  // mark the reserved entries left unused
+  const uint32_t nbb = __shfl_sync(full, nb, 0);
+  for (uint32_t k = cu + lane; k < DQ_CHUNK; k += 32) queue[cb + k] = make_uint4(0u, 0u, 0u, RES_HOLE);
+  for (uint32_t k = lane; k < DQ_CHUNK; k += 32) queue[nbb + k] = make_uint4(0u, 0u, 0u, RES_HOLE);
+  if (lane == 0 && wreal) atomicAdd(qcount + 2, wreal);
+}
+
 // ------------------------------------------------------------------- K2
 // Counting sort by superbin: off = exclusive scan of hist (in points).
 __global__ void k_scatter(const Residual* __restrict__ queue, const uint32_t* __restrict__ qcount,
@@ -80,6 +293,7 @@ __global__ void k_scatter(const Residual* __restrict__ queue, const uint32_t* __
   const uint32_t n = *qcount;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const Residual e = queue[i];
+    if (e.w == RES_HOLE) continue;
     const uint32_t sb = e.w >> SB_LOG2;
     const uint32_t pos = (uint32_t)off[sb] + atomicAdd(cursor + sb, 1u);
     binned[pos] = e;
@@ -264,6 +478,61 @@ pip_status k3_launch_public(const IndexView& ix, int stages, const Residual* bin
   return k3_launch(ix, stages, binned, qcount, ppc, item_ctr, out, status, s);
 }
 
+// K1 grid: one persistent wave of the deferred-queue kernel.
+static unsigned k1_grid(int64_t n) {
+  static int occ = 0;
+  if (!occ) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_classify_dq<true>, DQ_THREADS, 0) != cudaSuccess)
+      occ = 1;
+    occ = std::max(1, occ);
+  }
+  const int64_t groups = (n + 3) / 4;
+  return (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>((groups + DQ_THREADS - 1) / DQ_THREADS, (int64_t)num_sms() * occ));
+}
+
+// Queue entries K1 may use for n points: n plus two reserved chunks per warp.
+int64_t k1_queue_entries(int64_t n) {
+  return n + 2 * (int64_t)DQ_CHUNK * (DQ_THREADS / 32) * k1_grid(n);
+}
+
+// K1 over n points (deferred-queue form): 16-byte loads and stores when lon,
+// lat and out are 16-byte aligned, else scalar ones. qcount[0] counts queue
+// entries including holes, qcount[2] the residual points; the queue holds
+// k1_queue_entries(n) entries.
+cudaError_t k1_launch(const IndexView& ix, const double* lon, const double* lat, int64_t n,
+                      int32_t* out, Residual* queue, uint32_t* qcount, uint32_t* hist, cudaStream_t s) {
+  const bool vec = ((uintptr_t)lon % 16 == 0) && ((uintptr_t)lat % 16 == 0) && ((uintptr_t)out % 16 == 0);
+  const unsigned g1 = k1_grid(n);
+  if (vec)
+    k_classify_dq<true><<<g1, DQ_THREADS, 0, s>>>(ix, lon, lat, n, out, queue, qcount, hist);
+  else
+    k_classify_dq<false><<<g1, DQ_THREADS, 0, s>>>(ix, lon, lat, n, out, queue, qcount, hist);
+  return cudaGetLastError();
+}
+
+// K1 in the lockstep form: no reserved chunks, so the queue needs only n
+// entries and qcount[0] is the residual count.
+cudaError_t k1_launch_lockstep(const IndexView& ix, const double* lon, const double* lat, int64_t n,
+                               int32_t* out, Residual* queue, uint32_t* qcount, uint32_t* hist,
+                               cudaStream_t s) {
+  static int occ = 0;
+  if (!occ) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_classify_points<true>, K1_THREADS, 0);
+    if (e != cudaSuccess) return e;
+    occ = std::max(1, occ);
+  }
+  const bool vec = ((uintptr_t)lon % 16 == 0) && ((uintptr_t)lat % 16 == 0) && ((uintptr_t)out % 16 == 0);
+  const int64_t groups = (n + 3) / 4;
+  const unsigned g1 = (unsigned)std::max<int64_t>(
+      1, std::min<int64_t>((groups + K1_THREADS - 1) / K1_THREADS, (int64_t)num_sms() * occ));
+  if (vec)
+    k_classify_points<true><<<g1, K1_THREADS, 0, s>>>(ix, lon, lat, n, out, queue, qcount, hist);
+  else
+    k_classify_points<false><<<g1, K1_THREADS, 0, s>>>(ix, lon, lat, n, out, queue, qcount, hist);
+  return cudaGetLastError();
+}
+
 // Scratch of one device-resident projection of n points.
 struct ProjScratch {
   DBuf<Residual> queue, binned;
@@ -275,14 +544,15 @@ struct ProjScratch {
 pip_status project_device(pip_set_s* S, const double* lon, const double* lat, int64_t n, int32_t* out,
                           cudaStream_t s, pip_project_stats* stats) {
   if (n <= 0) return PIP_OK;
-  if (n >= (1ll << 32) - 1) return fail(PIP_EINVAL, "pip_project: n must be < 2^32 - 1 per device call");
+  if (n >= (1ll << 32) - 1 || k1_queue_entries(n) >= (1ll << 32))
+    return fail(PIP_EINVAL, "pip_project: too many points for one device call (queue indices are 32-bit)");
   init_pool_once();
   Alloc* al = &S->alloc;
   const IndexView& ix = S->view;
   const int64_t n_sb = std::max<int64_t>(1, ix.n_sb);
   const uint32_t ppc = (uint32_t)std::max(1, S->opts.pts_per_cta);
   ProjScratch w;
-  if (!w.queue.alloc(al, n, s) || !w.binned.alloc(al, n, s) || !w.hist.alloc(al, 2 * n_sb, s) ||
+  if (!w.queue.alloc(al, k1_queue_entries(n), s) || !w.binned.alloc(al, n, s) || !w.hist.alloc(al, 2 * n_sb, s) ||
       !w.off.alloc(al, n_sb, s) || !w.ctr.alloc(al, 4, s))
     return fail(PIP_ENOMEM, "pip_project: scratch allocation failed");
   uint32_t* hist = w.hist.p;
@@ -294,37 +564,24 @@ pip_status project_device(pip_set_s* S, const double* lon, const double* lat, in
   }
   PIP_CUDA(cudaMemsetAsync(w.hist.p, 0, 2 * n_sb * sizeof(uint32_t), s));
   PIP_CUDA(cudaMemsetAsync(w.ctr.p, 0, 4 * sizeof(uint32_t), s));
-  const bool vec = ((uintptr_t)lon % 16 == 0) && ((uintptr_t)lat % 16 == 0) && ((uintptr_t)out % 16 == 0);
-  const int64_t groups = (n + 3) / 4;
-  static int occ1 = 0;
-  if (!occ1) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_classify_points<true>, K1_THREADS, 0);
-    occ1 = std::max(1, occ1);
-  }
-  const unsigned g1 = (unsigned)std::max<int64_t>(
-      1, std::min<int64_t>((groups + K1_THREADS - 1) / K1_THREADS, (int64_t)num_sms() * occ1));
-  if (vec)
-    k_classify_points<true><<<g1, K1_THREADS, 0, s>>>(ix, lon, lat, n, out, w.queue.p, w.ctr.p, hist);
-  else
-    k_classify_points<false><<<g1, K1_THREADS, 0, s>>>(ix, lon, lat, n, out, w.queue.p, w.ctr.p, hist);
-  PIP_CUDA(cudaGetLastError());
+  PIP_CUDA(k1_launch(ix, lon, lat, n, out, w.queue.p, w.ctr.p, hist, s));
   if (prof >= 0) PIP_CUDA(cudaEventRecord(S->prof_ev[4 * prof + 1], s));
   pip_status st = scan_u32_to_u64(*al, hist, w.off.p, n_sb, nullptr, s);
   if (st != PIP_OK) return st;
   k_scatter<<<(unsigned)(num_sms() * 8), 256, 0, s>>>(w.queue.p, w.ctr.p, w.off.p, cursor, w.binned.p);
   PIP_CUDA(cudaGetLastError());
   if (prof >= 0) PIP_CUDA(cudaEventRecord(S->prof_ev[4 * prof + 2], s));
-  st = k3_launch(ix, S->opts.stage_depth, w.binned.p, w.ctr.p, ppc, w.ctr.p + 1, out, S->status.p, s);
+  st = k3_launch(ix, S->opts.stage_depth, w.binned.p, w.ctr.p + 2, ppc, w.ctr.p + 1, out, S->status.p, s);
   if (st != PIP_OK) return st;
   if (prof >= 0) PIP_CUDA(cudaEventRecord(S->prof_ev[4 * prof + 3], s));
   count_launches(3);  // K1, scatter, K3 (the scan counts its own)
   if (stats) {
-    uint32_t c[2];
+    uint32_t c[3];
     PIP_CUDA(cudaMemcpyAsync(c, w.ctr.p, sizeof(c), cudaMemcpyDeviceToHost, s));
     PIP_CUDA(cudaStreamSynchronize(s));
     stats->n = n;
-    stats->residual = c[0];
-    stats->items = (c[0] + ppc - 1) / ppc;
+    stats->residual = c[2];
+    stats->items = (c[2] + ppc - 1) / ppc;
   }
   return PIP_OK;
 }
@@ -342,17 +599,7 @@ pip_status project_device_scratch(pip_set_s* S, const double* lon, const double*
   const uint32_t ppc = (uint32_t)std::max(1, S->opts.pts_per_cta);
   PIP_CUDA(cudaMemsetAsync(hist2, 0, 2 * n_sb * sizeof(uint32_t), s));
   PIP_CUDA(cudaMemsetAsync(ctr, 0, 4 * sizeof(uint32_t), s));
-  const bool vec = ((uintptr_t)lon % 16 == 0) && ((uintptr_t)lat % 16 == 0) && ((uintptr_t)out % 16 == 0);
-  const int64_t groups = (n + 3) / 4;
-  int occ1 = 0;
-  PIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_classify_points<true>, K1_THREADS, 0));
-  const unsigned g1 = (unsigned)std::max<int64_t>(
-      1, std::min<int64_t>((groups + K1_THREADS - 1) / K1_THREADS, (int64_t)num_sms() * std::max(1, occ1)));
-  if (vec)
-    k_classify_points<true><<<g1, K1_THREADS, 0, s>>>(ix, lon, lat, n, out, queue, ctr, hist2);
-  else
-    k_classify_points<false><<<g1, K1_THREADS, 0, s>>>(ix, lon, lat, n, out, queue, ctr, hist2);
-  PIP_CUDA(cudaGetLastError());
+  PIP_CUDA(k1_launch_lockstep(ix, lon, lat, n, out, queue, ctr, hist2, s));
   pip_status st = scan_u32_to_u64_scratch(hist2, off, n_sb, scan_tmp, scan_len, s);
   if (st != PIP_OK) return st;
   k_scatter<<<(unsigned)(num_sms() * 8), 256, 0, s>>>(queue, ctr, off, hist2 + n_sb, binned);
