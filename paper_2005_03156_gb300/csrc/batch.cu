@@ -63,7 +63,7 @@ struct PlanBufs {
   uint32_t* cursor;       // [sb_cap]
   uint64_t* off;          // [sb_cap]
   uint64_t* partial;      // [grid + 1]
-  uint32_t* ctr;          // [0] qcount [1] tile ctr [2] chunk ctr [3] barrier count [4] barrier gen
+  uint32_t* ctr;          // [0] queue slots [1] tile ctr [2] chunk ctr [3] barrier count [4] barrier gen [5] residual count
   uint32_t* status;       // bounded-wait status word
 };
 
@@ -169,6 +169,7 @@ __global__ void __launch_bounds__(B_THREADS) k_batch(PlanBufs B) {
   __syncthreads();
 
   // ---- phase 0: classify tiles
+  ChunkWriter res;  // this warp's residual entries
   while (true) {
     if (threadIdx.x == 0) s_w = atomicAdd(B.ctr + 1, 1u);
     __syncthreads();
@@ -212,9 +213,13 @@ __global__ void __launch_bounds__(B_THREADS) k_batch(PlanBufs B) {
         for (int j = 0; j < 4; ++j)
           if (j0 + j < tl.z) out[j0 + j] = id[j];
       }
-      append_residual(mask, qx, qy, d, (w << TILE_LOG2) + j0, B.queue, B.ctr + 0, B.hist, slot_add);
+      const uint32_t code = (w << TILE_LOG2) + j0;
+      if (__any_sync(0xffffffffu, mask != 0u))
+        res.put(mask, qx, qy, d, [code](int j) { return code + (uint32_t)j; }, B.queue, B.ctr + 0, B.hist,
+                slot_add);
     }
   }
+  res.finish(B.queue, B.ctr + 5);
   grid_barrier(B, nblocks);
 
   // ---- phase 1: exclusive scan of hist[0, n_sb_total) over all CTAs
@@ -269,10 +274,12 @@ __global__ void __launch_bounds__(B_THREADS) k_batch(PlanBufs B) {
   }
   grid_barrier(B, nblocks);
 
-  // ---- phase 2: scatter by global superbin
-  const uint32_t n_res = *(volatile uint32_t*)(B.ctr + 0);
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_res; i += nblocks * blockDim.x) {
+  // ---- phase 2: scatter by global superbin (queue slots include holes)
+  const uint32_t n_slots = *(volatile uint32_t*)(B.ctr + 0);
+  const uint32_t n_res = *(volatile uint32_t*)(B.ctr + 5);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_slots; i += nblocks * blockDim.x) {
     const Residual r = B.queue[i];
+    if (r.w == RES_HOLE) continue;
     const uint32_t gsb = r.w >> SB_LOG2;
     B.binned[(uint32_t)B.off[gsb] + atomicAdd(B.cursor + gsb, 1u)] = r;
   }
@@ -458,7 +465,17 @@ extern "C" pip_status pip_plan_create(int64_t max_points, int32_t max_queries, v
   P->off_tiles = align_up(P->off_qoff + sizeof(uint32_t) * ((size_t)max_queries + 1), 256);
   P->tables_bytes = align_up(P->off_tiles + sizeof(uint4) * (size_t)P->max_tiles, 256);
   Alloc* al = &P->alloc;
-  if (!P->tables.alloc(al, P->tables_bytes, s) || !P->queue.alloc(al, max_points, s) ||
+  // queue: max_points plus two reserved chunks per warp of the largest grid
+  int occ0 = 0, occ1 = 0;
+  PIP_CUDA(cudaFuncSetAttribute(k_batch<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                batch_smem(1, P->stage_bytes)));
+  PIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k_batch<0>, B_THREADS, 0));
+  PIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_batch<1>, B_THREADS,
+                                                         batch_smem(1, P->stage_bytes)));
+  const int64_t queue_len =
+      max_points + 2 * (int64_t)QCHUNK * (B_THREADS / 32) * num_sms() * std::max(1, std::max(occ0, occ1));
+  if (queue_len >= (1ll << 32)) return fail(PIP_EINVAL, "pip_plan_create: max_points too large");
+  if (!P->tables.alloc(al, P->tables_bytes, s) || !P->queue.alloc(al, queue_len, s) ||
       !P->binned.alloc(al, max_points, s) || !P->ctr.alloc(al, 8, s) || !P->status.alloc(al, 2, s))
     return fail(PIP_ENOMEM, "pip_plan_create: device buffers");
   for (int i = 0; i < 2; ++i) {

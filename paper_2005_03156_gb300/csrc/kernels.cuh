@@ -115,6 +115,76 @@ __device__ __forceinline__ void append_residual(uint32_t mask, const int32_t (&q
                      hist, slot_add);
 }
 
+// Residual entries of one warp into queue chunks of QCHUNK entries. The first
+// chunk is reserved when the warp meets its first residual point; from then
+// on lane 0 holds the base of the next chunk, reserved one chunk ahead, so
+// an append waits on the queue counter only once per warp. (Atomics on one
+// address are serialised in L2: one per warp and step of 128 points cost as
+// much as a whole trie walk.) Entries reserved but not filled are marked
+// RES_HOLE at the end; the warp's residual count is added to *real then.
+// A warp holds at most 2 * QCHUNK unused entries, so the queue needs
+// n + 2 * QCHUNK * warps entries. All lanes of the warp call every method.
+constexpr uint32_t QCHUNK = 256;  // >= 128, the most one call appends
+
+struct ChunkWriter {
+  uint32_t cb = 0, cu = 0, nb = 0, real = 0;  // cb, cu, real: warp-uniform; nb: lane 0
+  bool have = false;                          // warp-uniform: a chunk is reserved
+
+  template <class IdxOf>
+  __device__ __forceinline__ void put(uint32_t mask, const int32_t (&qx)[4], const int32_t (&qy)[4],
+                                      const uint32_t (&d)[4], IdxOf idx_of, Residual* __restrict__ queue,
+                                      uint32_t* __restrict__ count, uint32_t* __restrict__ hist,
+                                      uint32_t slot_add) {
+    const uint32_t full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const uint32_t c = __popc(mask);
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(full, incl, o);
+      if (lane >= o) incl += t;
+    }
+    const uint32_t tot = __shfl_sync(full, incl, 31);
+    if (tot == 0u) return;
+    if (!have) {
+      uint32_t b = 0;
+      if (lane == 0) b = atomicAdd(count, QCHUNK);
+      cb = __shfl_sync(full, b, 0);
+      cu = 0;
+      if (lane == 0) nb = atomicAdd(count, QCHUNK);
+      have = true;
+    }
+    const uint32_t nbb = __shfl_sync(full, nb, 0);
+    uint32_t r = cu + incl - c;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if ((mask >> j) & 1u) {
+        const uint32_t slot = (d[j] & PAYLOAD_MASK) + slot_add;
+        const uint32_t at = r < QCHUNK ? cb + r : nbb + (r - QCHUNK);
+        queue[at] = make_uint4((uint32_t)qx[j], (uint32_t)qy[j], idx_of(j), slot);
+        atomicAdd(hist + (slot >> SB_LOG2), 1u);
+        ++r;
+      }
+    }
+    cu += tot;
+    real += tot;
+    if (cu >= QCHUNK) {  // the next chunk becomes current; reserve another
+      cb = nbb;
+      cu -= QCHUNK;
+      if (lane == 0) nb = atomicAdd(count, QCHUNK);
+    }
+  }
+
+  __device__ __forceinline__ void finish(Residual* __restrict__ queue, uint32_t* __restrict__ real_count) {
+    if (!have) return;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nbb = __shfl_sync(0xffffffffu, nb, 0);
+    for (uint32_t k = cu + lane; k < QCHUNK; k += 32) queue[cb + k] = make_uint4(0u, 0u, 0u, RES_HOLE);
+    for (uint32_t k = lane; k < QCHUNK; k += 32) queue[nbb + k] = make_uint4(0u, 0u, 0u, RES_HOLE);
+    if (lane == 0) atomicAdd(real_count, real);
+  }
+};
+
 // Classify 4 points; returns their ids (-1 for residual ones) and the
 // residual mask.
 __device__ __forceinline__ uint32_t classify4(const IndexView& ix, const double (&x)[4],

@@ -85,19 +85,13 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_classify_points(
 // the lanes stay converged. Ids of points resolved below the top grid are
 // stored one by one; their sectors were written by the step's 16-byte store
 // moments before and are still in L2. Residual points go straight to the
-// global queue into a chunk of DQ_CHUNK entries the warp reserved earlier;
-// the atomic that reserves the following chunk is issued as soon as the
-// current one is taken, so no trie level waits on it. Entries a warp
-// reserved but did not fill are marked RES_HOLE (K2 skips them); the real
-// residual count goes to qcount[2] once per warp at the end. (Atomics on one
-// shared address are serialised in L2: one per trie level per warp cost as
-// much as the whole walk.)
+// global queue through a ChunkWriter (per-warp chunks reserved one ahead;
+// holes are marked and skipped by K2; the residual count is qcount[2]).
 // Shared memory holds only the ring (17 KB a CTA): the rest of the SM's
 // 256 KB stays L1, which holds the sectors of the index loads in flight; a
 // larger carve-out measurably throttles them.
 constexpr int DQ_RING = 256;    // ring entries per warp (at most 255 are ever held)
 constexpr int DQ_THREADS = 128;
-constexpr uint32_t DQ_CHUNK = 256;  // >= 128, the most one step can queue
 
 template <bool VEC>
 __global__ void __launch_bounds__(DQ_THREADS, 6) k_classify_dq(
@@ -114,45 +108,7 @@ __global__ void __launch_bounds__(DQ_THREADS, 6) k_classify_dq(
   const uint64_t pol = policy_evict_last();
   const uint32_t m = (1u << NODE_K) - 1u;
 
-  // residual chunks: the current one [cb, cb + DQ_CHUNK) has cu entries used;
-  // lane 0 holds the base of the next one, reserved in advance
-  uint32_t nb = 0;
-  if (lane == 0) nb = atomicAdd(qcount, DQ_CHUNK);
-  uint32_t cb = __shfl_sync(full, nb, 0), cu = 0;
-  if (lane == 0) nb = atomicAdd(qcount, DQ_CHUNK);
-  uint32_t wreal = 0;  // residual points this warp queued
-
-  // append the slots in mask (boundary leaves) to the queue
-  auto put_leaves = [&](uint32_t mask, const int32_t(&qx)[4], const int32_t(&qy)[4],
-                        const uint32_t(&idx)[4], const uint32_t(&d)[4]) {
-    const uint32_t c = __popc(mask);
-    uint32_t incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t t = __shfl_up_sync(full, incl, o);
-      if (lane >= o) incl += t;
-    }
-    const uint32_t tot = __shfl_sync(full, incl, 31);
-    const uint32_t nbb = __shfl_sync(full, nb, 0);  // waits only if the reservation is still in flight
-    uint32_t r = cu + incl - c;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if ((mask >> j) & 1u) {
-        const uint32_t slot = d[j] & PAYLOAD_MASK;
-        const uint32_t at = r < DQ_CHUNK ? cb + r : nbb + (r - DQ_CHUNK);
-        queue[at] = make_uint4((uint32_t)qx[j], (uint32_t)qy[j], idx[j], slot);
-        atomicAdd(hist + (slot >> SB_LOG2), 1u);
-        ++r;
-      }
-    }
-    cu += tot;
-    if (cu >= DQ_CHUNK) {  // the next chunk becomes current; reserve another
-      cb = nbb;
-      cu -= DQ_CHUNK;
-      if (lane == 0) nb = atomicAdd(qcount, DQ_CHUNK);
-    }
-    wreal += tot;
-  };
+  ChunkWriter res;  // residual entries of this warp
 
   // append the slots in mask (split cells: node d, child shift sh) to the ring
   auto push = [&](uint32_t mask, const int32_t(&qx)[4], const int32_t(&qy)[4], const uint32_t(&idx)[4],
@@ -221,7 +177,8 @@ __global__ void __launch_bounds__(DQ_THREADS, 6) k_classify_dq(
         sh[j] -= NODE_K;
       }
     }
-    if (__any_sync(full, leaf != 0u)) put_leaves(leaf, qx, qy, idx, d);
+    if (__any_sync(full, leaf != 0u))
+      res.put(leaf, qx, qy, d, [&](int j) { return idx[j]; }, queue, qcount, hist, 0u);
     if (__any_sync(full, again != 0u)) push(again, qx, qy, idx, d, sh);
   };
 
@@ -271,18 +228,15 @@ __global__ void __launch_bounds__(DQ_THREADS, 6) k_classify_dq(
       for (int j = 0; j < 4; ++j)
         if (i0 + j < n) out[i0 + j] = id[j];
     }
-    if (__any_sync(full, leaf != 0u)) put_leaves(leaf, qx, qy, idx, d);
+    if (__any_sync(full, leaf != 0u))
+      res.put(leaf, qx, qy, d, [&](int j) { return idx[j]; }, queue, qcount, hist, 0u);
     if (__any_sync(full, split != 0u)) push(split, qx, qy, idx, d, sh);
 #pragma unroll 1
     while (count >= 128u) step_ring(128u);
   }
 #pragma unroll 1
   while (count > 0u) step_ring(count < 128u ? count : 128u);
-  // mark the reserved entries left unused
-  const uint32_t nbb = __shfl_sync(full, nb, 0);
-  for (uint32_t k = cu + lane; k < DQ_CHUNK; k += 32) queue[cb + k] = make_uint4(0u, 0u, 0u, RES_HOLE);
-  for (uint32_t k = lane; k < DQ_CHUNK; k += 32) queue[nbb + k] = make_uint4(0u, 0u, 0u, RES_HOLE);
-  if (lane == 0 && wreal) atomicAdd(qcount + 2, wreal);
+  res.finish(queue, qcount + 2);
 }
 
 // ------------------------------------------------------------------- K2
@@ -493,7 +447,7 @@ static unsigned k1_grid(int64_t n) {
 
 // Queue entries K1 may use for n points: n plus two reserved chunks per warp.
 int64_t k1_queue_entries(int64_t n) {
-  return n + 2 * (int64_t)DQ_CHUNK * (DQ_THREADS / 32) * k1_grid(n);
+  return n + 2 * (int64_t)QCHUNK * (DQ_THREADS / 32) * k1_grid(n);
 }
 
 // K1 over n points (deferred-queue form): 16-byte loads and stores when lon,
