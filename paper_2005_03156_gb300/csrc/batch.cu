@@ -152,10 +152,10 @@ __device__ __forceinline__ void batch_test_chunk(const DevSet* sets, uint32_t n_
 }
 
 template <int STAGED>
-__global__ void __launch_bounds__(B_THREADS) k_batch(PlanBufs B) {
+__global__ void __launch_bounds__(B_THREADS, 3) k_batch(PlanBufs B) {
   extern __shared__ __align__(128) uint4 stage_mem[];
   __shared__ __align__(8) uint64_t bar;
-  __shared__ uint32_t s_w, s_staged, s_region;
+  __shared__ uint32_t s_w, s_staged, s_region;  // phase 3
   __shared__ DevSet s_sets[MAX_SETS];
   __shared__ uint64_t s_scan[B_THREADS / 32];
   const uint32_t nblocks = gridDim.x;
@@ -168,58 +168,108 @@ __global__ void __launch_bounds__(B_THREADS) k_batch(PlanBufs B) {
   }
   __syncthreads();
 
-  // ---- phase 0: classify tiles
-  ChunkWriter res;  // this warp's residual entries
-  while (true) {
-    if (threadIdx.x == 0) s_w = atomicAdd(B.ctr + 1, 1u);
-    __syncthreads();
-    const uint32_t w = s_w;
-    __syncthreads();
-    if (w >= H.n_tiles) break;
-    const uint4 tl = B.tiles[w];  // (query, start, count, global offset)
-    const DevQuery q = B.queries[tl.x];
-    const DevSet& S = s_sets[q.set];
-    const uint32_t slot_add = S.sb_base << SB_LOG2;
-    const double* lon = q.lon + tl.y;
-    const double* lat = q.lat + tl.y;
-    int32_t* out = q.out + tl.y;
-    // 16-byte loads / stores when the tile's three arrays are aligned
-    const bool vec = (((uintptr_t)lon | (uintptr_t)lat | (uintptr_t)out) & 15u) == 0;
-    for (uint32_t g0 = 0; g0 < tl.z; g0 += 4 * blockDim.x) {
-      const uint32_t j0 = g0 + 4 * threadIdx.x;  // offset within the tile
-      double x[4], y[4];
-      if (vec && j0 + 3 < tl.z) {
-        const double2 a0 = __ldcs(reinterpret_cast<const double2*>(lon + j0));
-        const double2 a1 = __ldcs(reinterpret_cast<const double2*>(lon + j0) + 1);
-        const double2 b0 = __ldcs(reinterpret_cast<const double2*>(lat + j0));
-        const double2 b1 = __ldcs(reinterpret_cast<const double2*>(lat + j0) + 1);
-        x[0] = a0.x; x[1] = a0.y; x[2] = a1.x; x[3] = a1.y;
-        y[0] = b0.x; y[1] = b0.y; y[2] = b1.x; y[3] = b1.y;
-      } else {
+  // ---- phase 0: classify tiles. Each warp takes whole tiles: a step reads
+  // the top-grid descriptors of 128 points, points in split cells wait in the
+  // warp's trie ring (walked one level for 128 entries at a time) and the ring
+  // is drained at the end of the tile, so its entries share the tile's set and
+  // output array.
+  {
+    __shared__ uint4 ring[B_THREADS / 32][TRING];
+    __shared__ uint8_t ring_sh[B_THREADS / 32][TRING];
+    const uint32_t full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const uint64_t pol = policy_evict_last();
+    TrieRing tr;
+    tr.rq = ring[threadIdx.x >> 5];
+    tr.rs = ring_sh[threadIdx.x >> 5];
+    ChunkWriter res;  // this warp's residual entries
+    while (true) {
+      uint32_t w = 0;
+      if (lane == 0) w = atomicAdd(B.ctr + 1, 1u);
+      w = __shfl_sync(full, w, 0);
+      if (w >= H.n_tiles) break;
+      const uint4 tl = B.tiles[w];  // (query, start, count, global offset)
+      const DevQuery q = B.queries[tl.x];
+      const DevSet& S = s_sets[q.set];
+      const IndexView& ix = S.view;
+      const uint32_t slot_add = S.sb_base << SB_LOG2;
+      const uint32_t code0 = w << TILE_LOG2;
+      const double* lon = q.lon + tl.y;
+      const double* lat = q.lat + tl.y;
+      int32_t* out = q.out + tl.y;
+      // 16-byte loads / stores when the tile's three arrays are aligned
+      const bool vec = (((uintptr_t)lon | (uintptr_t)lat | (uintptr_t)out) & 15u) == 0;
+      auto load = [&](uint32_t j0, double(&x)[4], double(&y)[4]) {
+        if (vec && j0 + 3 < tl.z) {
+          const double2 a0 = __ldcs(reinterpret_cast<const double2*>(lon + j0));
+          const double2 a1 = __ldcs(reinterpret_cast<const double2*>(lon + j0) + 1);
+          const double2 b0 = __ldcs(reinterpret_cast<const double2*>(lat + j0));
+          const double2 b1 = __ldcs(reinterpret_cast<const double2*>(lat + j0) + 1);
+          x[0] = a0.x; x[1] = a0.y; x[2] = a1.x; x[3] = a1.y;
+          y[0] = b0.x; y[1] = b0.y; y[2] = b1.x; y[3] = b1.y;
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const bool have = j0 + j < tl.z;
+            x[j] = have ? __ldcs(lon + j0 + j) : __longlong_as_double(0x7FF8000000000000ll);
+            y[j] = have ? __ldcs(lat + j0 + j) : 0.0;
+          }
+        }
+      };
+      double nx[4], ny[4];
+      load(4 * lane, nx, ny);
+#pragma unroll 1
+      for (uint32_t g0 = 0; g0 < tl.z; g0 += 128u) {
+        const uint32_t j0 = g0 + 4 * lane;  // offset within the tile
+        double x[4], y[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const bool have = j0 + j < tl.z;
-          x[j] = have ? __ldcs(lon + j0 + j) : __longlong_as_double(0x7FF8000000000000ll);
-          y[j] = have ? __ldcs(lat + j0 + j) : 0.0;
+          x[j] = nx[j];
+          y[j] = ny[j];
         }
-      }
-      int32_t id[4], qx[4], qy[4];
-      uint32_t d[4];
-      const uint32_t mask = classify4(S.view, x, y, id, qx, qy, d);
-      if (vec && j0 + 3 < tl.z) {
-        __stcs(reinterpret_cast<int4*>(out + j0), make_int4(id[0], id[1], id[2], id[3]));
-      } else {
+        if (g0 + 128u < tl.z) load(j0 + 128u, nx, ny);
+        int32_t qx[4], qy[4], id[4];
+        uint32_t d[4], z[4];
+        int sh[4];
+        const uint32_t s0 = (uint32_t)ix.s0;
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (j0 + j < tl.z) out[j0 + j] = id[j];
+        for (int j = 0; j < 4; ++j) {
+          qx[j] = qy[j] = 0;
+          const bool ok = quantize_double(x[j], qx[j]) & quantize_double(y[j], qy[j]);
+          const uint32_t dx = (uint32_t)qx[j] - (uint32_t)ix.gx0, dy = (uint32_t)qy[j] - (uint32_t)ix.gy0;
+          const uint32_t cx = dx >> s0, cy = dy >> s0;
+          const bool in = ok & (cx < ix.nx) & (cy < ix.ny) & (qx[j] >= ix.gx0) & (qy[j] >= ix.gy0);
+          d[j] = in ? ld_index_u32(ix.table + (size_t)cy * ix.nx + cx, pol) : 0u;
+          z[j] = j0 + j;
+          sh[j] = (int)s0 - NODE_K;
+        }
+        uint32_t leaf = 0, split = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const uint32_t tag = d[j] >> 30;
+          id[j] = tag == TAG_INTERIOR ? (int32_t)(d[j] & PAYLOAD_MASK) : -1;
+          leaf |= (tag == TAG_LEAF ? 1u : 0u) << j;
+          split |= (tag == TAG_CHILD ? 1u : 0u) << j;
+        }
+        if (vec && j0 + 3 < tl.z) {
+          *reinterpret_cast<int4*>(out + j0) = make_int4(id[0], id[1], id[2], id[3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (j0 + j < tl.z) out[j0 + j] = id[j];
+        }
+        if (__any_sync(full, leaf != 0u))
+          res.put(leaf, qx, qy, d, [&](int j) { return code0 + z[j]; }, B.queue, B.ctr + 0, B.hist, slot_add);
+        if (__any_sync(full, split != 0u)) tr.push(split, qx, qy, z, d, sh);
+#pragma unroll 1
+        while (tr.count >= 128u) tr.step(128u, ix, pol, out, code0, res, B.queue, B.ctr + 0, B.hist, slot_add);
       }
-      const uint32_t code = (w << TILE_LOG2) + j0;
-      if (__any_sync(0xffffffffu, mask != 0u))
-        res.put(mask, qx, qy, d, [code](int j) { return code + (uint32_t)j; }, B.queue, B.ctr + 0, B.hist,
-                slot_add);
+#pragma unroll 1
+      while (tr.count > 0u)
+        tr.step(tr.count < 128u ? tr.count : 128u, ix, pol, out, code0, res, B.queue, B.ctr + 0, B.hist, slot_add);
     }
+    res.finish(B.queue, B.ctr + 5);
   }
-  res.finish(B.queue, B.ctr + 5);
   grid_barrier(B, nblocks);
 
   // ---- phase 1: exclusive scan of hist[0, n_sb_total) over all CTAs

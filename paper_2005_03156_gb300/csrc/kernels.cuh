@@ -185,6 +185,102 @@ struct ChunkWriter {
   }
 };
 
+// Per-warp ring of points whose cell is split (K1, deferred-queue form): a
+// step reads the top-grid descriptors of 4 points per lane and pushes the
+// split ones here; step() then walks one trie level for up to 128 entries at
+// once (4 per lane), stores INTERIOR ids, hands boundary leaves to the
+// residual writer and pushes back the entries still split. Entry: (qx, qy, z,
+// node) plus the shift of the node's children; the point's id goes to
+// out_base[z] and its residual index is code_base + z. The ring lives in
+// shared memory (TRING entries, at most TRING - 1 held); all lanes call.
+constexpr uint32_t TRING = 256;
+
+struct TrieRing {
+  uint4* rq;
+  uint8_t* rs;
+  uint32_t head = 0, count = 0;  // warp-uniform
+
+  __device__ __forceinline__ void push(uint32_t mask, const int32_t (&qx)[4], const int32_t (&qy)[4],
+                                       const uint32_t (&z)[4], const uint32_t (&d)[4], const int (&sh)[4]) {
+    const uint32_t full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const uint32_t c = __popc(mask);
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(full, incl, o);
+      if (lane >= o) incl += t;
+    }
+    uint32_t pos = head + count + incl - c;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if ((mask >> j) & 1u) {
+        const uint32_t p = pos++ & (TRING - 1);
+        rq[p] = make_uint4((uint32_t)qx[j], (uint32_t)qy[j], z[j], d[j] & PAYLOAD_MASK);
+        rs[p] = (uint8_t)sh[j];
+      }
+    }
+    count += __shfl_sync(full, incl, 31);
+  }
+
+  // one trie level for the ring's first `take` entries (take <= 128, uniform)
+  __device__ __forceinline__ void step(uint32_t take, const IndexView& ix, uint64_t pol,
+                                       int32_t* __restrict__ out_base, uint32_t code_base,
+                                       ChunkWriter& res, Residual* __restrict__ queue,
+                                       uint32_t* __restrict__ qcount, uint32_t* __restrict__ hist,
+                                       uint32_t slot_add) {
+    const uint32_t full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const uint32_t m = (1u << NODE_K) - 1u;
+    __syncwarp();
+    int32_t qx[4], qy[4];
+    uint32_t z[4], d[4];
+    int sh[4];
+    uint32_t have = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t k = (uint32_t)lane + 32u * j;
+      qx[j] = qy[j] = 0;
+      z[j] = d[j] = 0u;
+      sh[j] = 0;
+      if (k < take) {
+        const uint32_t p = (head + k) & (TRING - 1);
+        const uint4 e = rq[p];
+        qx[j] = (int32_t)e.x;
+        qy[j] = (int32_t)e.y;
+        z[j] = e.z;
+        d[j] = e.w;
+        sh[j] = rs[p];
+        have |= 1u << j;
+      }
+    }
+    head += take;
+    count -= take;
+    __syncwarp();  // every entry is read before the pushes below reuse slots
+    NodeWords nw[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if ((have >> j) & 1u) nw[j] = ld_node(ix.nodes, d[j], pol);
+    uint32_t leaf = 0, again = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if ((have >> j) & 1u) {
+        const uint32_t dx = (uint32_t)qx[j] - (uint32_t)ix.gx0, dy = (uint32_t)qy[j] - (uint32_t)ix.gy0;
+        const uint32_t sub = (((dy >> sh[j]) & m) << NODE_K) | ((dx >> sh[j]) & m);
+        d[j] = node_step(nw[j], sub);
+        const uint32_t tag = d[j] >> 30;
+        if (tag == TAG_INTERIOR) out_base[z[j]] = (int32_t)(d[j] & PAYLOAD_MASK);
+        leaf |= (tag == TAG_LEAF ? 1u : 0u) << j;
+        again |= (tag == TAG_CHILD ? 1u : 0u) << j;
+        sh[j] -= NODE_K;
+      }
+    }
+    if (__any_sync(full, leaf != 0u))
+      res.put(leaf, qx, qy, d, [&](int j) { return code_base + z[j]; }, queue, qcount, hist, slot_add);
+    if (__any_sync(full, again != 0u)) push(again, qx, qy, z, d, sh);
+  }
+};
+
 // Classify 4 points; returns their ids (-1 for residual ones) and the
 // residual mask.
 __device__ __forceinline__ uint32_t classify4(const IndexView& ix, const double (&x)[4],

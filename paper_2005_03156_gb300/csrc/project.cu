@@ -90,7 +90,6 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_classify_points(
 // Shared memory holds only the ring (17 KB a CTA): the rest of the SM's
 // 256 KB stays L1, which holds the sectors of the index loads in flight; a
 // larger carve-out measurably throttles them.
-constexpr int DQ_RING = 256;    // ring entries per warp (at most 255 are ever held)
 constexpr int DQ_THREADS = 128;
 
 template <bool VEC>
@@ -98,89 +97,14 @@ __global__ void __launch_bounds__(DQ_THREADS, 6) k_classify_dq(
     IndexView ix, const double* __restrict__ lon, const double* __restrict__ lat, int64_t n,
     int32_t* __restrict__ out, Residual* __restrict__ queue, uint32_t* __restrict__ qcount,
     uint32_t* __restrict__ hist) {
-  __shared__ uint4 ring[DQ_THREADS / 32][DQ_RING];      // (qx, qy, point, node)
-  __shared__ uint8_t ring_sh[DQ_THREADS / 32][DQ_RING];  // shift of the node's children
+  __shared__ uint4 ring[DQ_THREADS / 32][TRING];
+  __shared__ uint8_t ring_sh[DQ_THREADS / 32][TRING];
   const uint32_t full = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  uint4* rq = ring[threadIdx.x >> 5];
-  uint8_t* rs = ring_sh[threadIdx.x >> 5];
-  uint32_t head = 0, count = 0;  // warp-uniform
   const uint64_t pol = policy_evict_last();
-  const uint32_t m = (1u << NODE_K) - 1u;
-
+  TrieRing tr;
+  tr.rq = ring[threadIdx.x >> 5];
+  tr.rs = ring_sh[threadIdx.x >> 5];
   ChunkWriter res;  // residual entries of this warp
-
-  // append the slots in mask (split cells: node d, child shift sh) to the ring
-  auto push = [&](uint32_t mask, const int32_t(&qx)[4], const int32_t(&qy)[4], const uint32_t(&idx)[4],
-                  const uint32_t(&d)[4], const int(&sh)[4]) {
-    const uint32_t c = __popc(mask);
-    uint32_t incl = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t t = __shfl_up_sync(full, incl, o);
-      if (lane >= o) incl += t;
-    }
-    uint32_t pos = head + count + incl - c;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if ((mask >> j) & 1u) {
-        const uint32_t p = pos++ & (DQ_RING - 1);
-        rq[p] = make_uint4((uint32_t)qx[j], (uint32_t)qy[j], idx[j], d[j] & PAYLOAD_MASK);
-        rs[p] = (uint8_t)sh[j];
-      }
-    }
-    count += __shfl_sync(full, incl, 31);
-  };
-
-  // one trie level for the ring's first `take` entries (take <= 128, uniform)
-  auto step_ring = [&](uint32_t take) {
-    __syncwarp();
-    int32_t qx[4], qy[4];
-    uint32_t idx[4], d[4];
-    int sh[4];
-    uint32_t have = 0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint32_t k = (uint32_t)lane + 32u * j;
-      qx[j] = qy[j] = 0;
-      idx[j] = d[j] = 0u;
-      sh[j] = 0;
-      if (k < take) {
-        const uint32_t p = (head + k) & (DQ_RING - 1);
-        const uint4 e = rq[p];
-        qx[j] = (int32_t)e.x;
-        qy[j] = (int32_t)e.y;
-        idx[j] = e.z;
-        d[j] = e.w;
-        sh[j] = rs[p];
-        have |= 1u << j;
-      }
-    }
-    head += take;
-    count -= take;
-    __syncwarp();  // every entry is read before the pushes below reuse slots
-    NodeWords nw[4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if ((have >> j) & 1u) nw[j] = ld_node(ix.nodes, d[j], pol);
-    uint32_t leaf = 0, again = 0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      if ((have >> j) & 1u) {
-        const uint32_t dx = (uint32_t)qx[j] - (uint32_t)ix.gx0, dy = (uint32_t)qy[j] - (uint32_t)ix.gy0;
-        const uint32_t sub = (((dy >> sh[j]) & m) << NODE_K) | ((dx >> sh[j]) & m);
-        d[j] = node_step(nw[j], sub);
-        const uint32_t tag = d[j] >> 30;
-        if (tag == TAG_INTERIOR) out[idx[j]] = (int32_t)(d[j] & PAYLOAD_MASK);
-        leaf |= (tag == TAG_LEAF ? 1u : 0u) << j;
-        again |= (tag == TAG_CHILD ? 1u : 0u) << j;
-        sh[j] -= NODE_K;
-      }
-    }
-    if (__any_sync(full, leaf != 0u))
-      res.put(leaf, qx, qy, d, [&](int j) { return idx[j]; }, queue, qcount, hist, 0u);
-    if (__any_sync(full, again != 0u)) push(again, qx, qy, idx, d, sh);
-  };
 
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -230,12 +154,12 @@ __global__ void __launch_bounds__(DQ_THREADS, 6) k_classify_dq(
     }
     if (__any_sync(full, leaf != 0u))
       res.put(leaf, qx, qy, d, [&](int j) { return idx[j]; }, queue, qcount, hist, 0u);
-    if (__any_sync(full, split != 0u)) push(split, qx, qy, idx, d, sh);
+    if (__any_sync(full, split != 0u)) tr.push(split, qx, qy, idx, d, sh);
 #pragma unroll 1
-    while (count >= 128u) step_ring(128u);
+    while (tr.count >= 128u) tr.step(128u, ix, pol, out, 0u, res, queue, qcount, hist, 0u);
   }
 #pragma unroll 1
-  while (count > 0u) step_ring(count < 128u ? count : 128u);
+  while (tr.count > 0u) tr.step(tr.count < 128u ? tr.count : 128u, ix, pol, out, 0u, res, queue, qcount, hist, 0u);
   res.finish(queue, qcount + 2);
 }
 
