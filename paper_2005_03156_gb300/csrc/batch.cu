@@ -48,7 +48,8 @@ struct DevQuery {
 // Layout of the per-run table block (host pinned -> device in one copy).
 struct RunHeader {
   uint32_t n_q, n_sets, n_tiles, total_points;
-  uint32_t n_sb_total, ppc, stage16, pad;
+  uint32_t n_sb_total, ppc, stage16;
+  uint32_t sub_log2;  // phase-0 work item: 2^sub_log2 points of a tile (10..12)
 };
 
 struct PlanBufs {
@@ -168,11 +169,13 @@ __global__ void __launch_bounds__(B_THREADS, 3) k_batch(PlanBufs B) {
   }
   __syncthreads();
 
-  // ---- phase 0: classify tiles. Each warp takes whole tiles: a step reads
-  // the top-grid descriptors of 128 points, points in split cells wait in the
-  // warp's trie ring (walked one level for 128 entries at a time) and the ring
-  // is drained at the end of the tile, so its entries share the tile's set and
-  // output array.
+  // ---- phase 0: classify tiles. Each warp takes work items of 2^sub_log2
+  // points of one tile: a step reads the top-grid descriptors of 128 points,
+  // points in split cells wait in the warp's trie ring (walked one level for
+  // 128 entries at a time) and the ring is drained at the end of the item, so
+  // its entries share the tile's set and output array. Large batches use
+  // whole tiles (fewer drains); small ones 1024-point items (whole tiles per
+  // warp made a small batch's latency 4x that of a CTA-wide tile).
   {
     __shared__ uint4 ring[B_THREADS / 32][TRING];
     __shared__ uint8_t ring_sh[B_THREADS / 32][TRING];
@@ -184,11 +187,16 @@ __global__ void __launch_bounds__(B_THREADS, 3) k_batch(PlanBufs B) {
     tr.rs = ring_sh[threadIdx.x >> 5];
     ChunkWriter res;  // this warp's residual entries
     while (true) {
-      uint32_t w = 0;
-      if (lane == 0) w = atomicAdd(B.ctr + 1, 1u);
-      w = __shfl_sync(full, w, 0);
-      if (w >= H.n_tiles) break;
+      uint32_t item = 0;
+      if (lane == 0) item = atomicAdd(B.ctr + 1, 1u);
+      item = __shfl_sync(full, item, 0);
+      const uint32_t per_tile_log2 = TILE_LOG2 - H.sub_log2;
+      if (item >= (H.n_tiles << per_tile_log2)) break;
+      const uint32_t w = item >> per_tile_log2;
       const uint4 tl = B.tiles[w];  // (query, start, count, global offset)
+      const uint32_t g_begin = (item & ((1u << per_tile_log2) - 1u)) << H.sub_log2;
+      if (g_begin >= tl.z) continue;
+      const uint32_t g_end = min(tl.z, g_begin + (1u << H.sub_log2));
       const DevQuery q = B.queries[tl.x];
       const DevSet& S = s_sets[q.set];
       const IndexView& ix = S.view;
@@ -217,9 +225,9 @@ __global__ void __launch_bounds__(B_THREADS, 3) k_batch(PlanBufs B) {
         }
       };
       double nx[4], ny[4];
-      load(4 * lane, nx, ny);
+      load(g_begin + 4 * lane, nx, ny);
 #pragma unroll 1
-      for (uint32_t g0 = 0; g0 < tl.z; g0 += 128u) {
+      for (uint32_t g0 = g_begin; g0 < g_end; g0 += 128u) {
         const uint32_t j0 = g0 + 4 * lane;  // offset within the tile
         double x[4], y[4];
 #pragma unroll
@@ -227,7 +235,7 @@ __global__ void __launch_bounds__(B_THREADS, 3) k_batch(PlanBufs B) {
           x[j] = nx[j];
           y[j] = ny[j];
         }
-        if (g0 + 128u < tl.z) load(j0 + 128u, nx, ny);
+        if (g0 + 128u < g_end) load(j0 + 128u, nx, ny);
         int32_t qx[4], qy[4], id[4];
         uint32_t d[4], z[4];
         int sh[4];
@@ -327,12 +335,8 @@ __global__ void __launch_bounds__(B_THREADS, 3) k_batch(PlanBufs B) {
   // ---- phase 2: scatter by global superbin (queue slots include holes)
   const uint32_t n_slots = *(volatile uint32_t*)(B.ctr + 0);
   const uint32_t n_res = *(volatile uint32_t*)(B.ctr + 5);
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n_slots; i += nblocks * blockDim.x) {
-    const Residual r = B.queue[i];
-    if (r.w == RES_HOLE) continue;
-    const uint32_t gsb = r.w >> SB_LOG2;
-    B.binned[(uint32_t)B.off[gsb] + atomicAdd(B.cursor + gsb, 1u)] = r;
-  }
+  scatter_by_superbin(B.queue, n_slots, B.off, B.cursor, B.binned, blockIdx.x * blockDim.x + threadIdx.x,
+                      nblocks * blockDim.x);
   grid_barrier(B, nblocks);
 
   // ---- phase 3: crossing tests, chunks of ppc binned points
@@ -622,6 +626,9 @@ extern "C" pip_status pip_plan_run(pip_plan plan, const pip_query* q, int32_t n_
   H.n_sets = (uint32_t)sets.size();
   H.n_tiles = n_tiles;
   H.total_points = acc;
+  // whole tiles per warp when every warp gets several (the ring drains once
+  // per item); 1024-point items for small batches, whose latency is one item
+  H.sub_log2 = (int64_t)acc >= (int64_t)plan->grid * (B_THREADS / 32) * 4 * TILE ? 12u : 10u;
   H.n_sb_total = (uint32_t)sb_total;
   H.ppc = plan->ppc;
   H.stage16 = plan->stage_bytes / 16;

@@ -281,6 +281,22 @@ struct TrieRing {
   }
 };
 
+// K2 body: queue entries [0, n) go to binned[off[sb] + rank], rank taken from
+// cursor[sb]; RES_HOLE entries are skipped. (Four entries per thread with
+// their atomics issued back to back measured slower: 0.29 vs 0.27 ms.)
+__device__ __forceinline__ void scatter_by_superbin(const Residual* __restrict__ queue, uint32_t n,
+                                                    const uint64_t* __restrict__ off,
+                                                    uint32_t* __restrict__ cursor,
+                                                    Residual* __restrict__ binned, uint32_t tid,
+                                                    uint32_t stride) {
+  for (uint64_t i = tid; i < n; i += stride) {
+    const Residual e = queue[i];
+    if (e.w == RES_HOLE) continue;
+    const uint32_t sb = e.w >> SB_LOG2;
+    binned[(uint32_t)off[sb] + atomicAdd(cursor + sb, 1u)] = e;
+  }
+}
+
 // Classify 4 points; returns their ids (-1 for residual ones) and the
 // residual mask.
 __device__ __forceinline__ uint32_t classify4(const IndexView& ix, const double (&x)[4],
@@ -412,46 +428,53 @@ __device__ __forceinline__ uint32_t leaf_edges(const BlobView& b, uint32_t local
   return estart[b.words[local + 1]] - estart[b.words[local]];
 }
 
-// Test the residual points [first, first + count) of one work item. Each
-// point's superbin record lives either in the staged copy of the chunk's
-// contiguous record range (staged != nullptr, starting at 16-byte unit
-// region16 of the blobs) or in global memory. Ids go through `store`.
+// Crossing tests of the binned residual points [first, first + count),
+// count <= 32, one per lane of the calling warp. Each point's superbin record
+// lives either in the staged copy of the chunk's contiguous record range
+// (staged != nullptr, starting at 16-byte unit region16 of the blobs) or in
+// global memory. Points whose leaf holds a long edge list are tested by the
+// whole warp. Ids go through `store`.
+template <class Store>
+__device__ __forceinline__ void test_warp_slice(const IndexView& ix, const Residual* __restrict__ binned,
+                                                uint32_t first, uint32_t count, const uint4* staged,
+                                                uint32_t region16, Store store) {
+  const int lane = threadIdx.x & 31;
+  const bool active = (uint32_t)lane < count;
+  Residual r = make_uint4(0, 0, 0, 0);
+  const uint4* bp = ix.blobs;
+  if (active) {
+    r = binned[first + lane];
+    const uint2 sd = ix.sbdesc[r.w >> SB_LOG2];
+    bp = staged ? staged + (sd.x - region16) : ix.blobs + sd.x;
+  }
+  BlobView b{nullptr, nullptr};
+  if (active) b = blob_view(bp);
+  const uint32_t local = r.w & (SB_SLOTS - 1);
+  const bool is_long = active && leaf_edges(b, local) > (uint32_t)LONG_LIST;
+  int32_t id = -1;
+  if (active && !is_long) id = test_point(b, local, (int32_t)r.x, (int32_t)r.y);
+  uint32_t lm = __ballot_sync(0xffffffffu, is_long);
+  while (lm) {
+    const int j = __ffs(lm) - 1;
+    lm &= lm - 1;
+    const int32_t px = (int32_t)__shfl_sync(0xffffffffu, r.x, j);
+    const int32_t py = (int32_t)__shfl_sync(0xffffffffu, r.y, j);
+    const uint32_t lj = __shfl_sync(0xffffffffu, local, j);
+    const unsigned long long pj = __shfl_sync(0xffffffffu, (unsigned long long)(uintptr_t)bp, j);
+    const int32_t v = test_point_warp(blob_view((const uint4*)(uintptr_t)pj), lj, px, py);
+    if (lane == j) id = v;
+  }
+  if (active) store(r, id);
+}
+
+// Test the residual points [first, first + count) of one work item: the
+// CTA's warps take 32-point slices of it.
 template <class Store>
 __device__ __forceinline__ void test_chunk(const IndexView& ix, const Residual* __restrict__ binned,
                                            uint32_t first, uint32_t count, const uint4* staged,
                                            uint32_t region16, Store store) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t warp_base = (threadIdx.x & ~31u);
-  for (uint32_t base = warp_base; base < count; base += blockDim.x) {
-    const uint32_t t = base + lane;
-    const bool active = t < count;
-    Residual r = make_uint4(0, 0, 0, 0);
-    const uint4* bp = ix.blobs;
-    if (active) {
-      r = binned[first + t];
-      const uint2 sd = ix.sbdesc[r.w >> SB_LOG2];
-      bp = staged ? staged + (sd.x - region16) : ix.blobs + sd.x;
-    }
-    BlobView b{nullptr, nullptr};
-    if (active) b = blob_view(bp);
-    const uint32_t local = r.w & (SB_SLOTS - 1);
-    const bool is_long = active && leaf_edges(b, local) > (uint32_t)LONG_LIST;
-    int32_t id = -1;
-    if (active && !is_long) id = test_point(b, local, (int32_t)r.x, (int32_t)r.y);
-    uint32_t lm = __ballot_sync(0xffffffffu, is_long);
-    while (lm) {
-      const int j = __ffs(lm) - 1;
-      lm &= lm - 1;
-      const int32_t px = (int32_t)__shfl_sync(0xffffffffu, r.x, j);
-      const int32_t py = (int32_t)__shfl_sync(0xffffffffu, r.y, j);
-      const uint32_t lj = __shfl_sync(0xffffffffu, local, j);
-      const unsigned long long pj =
-          __shfl_sync(0xffffffffu, (unsigned long long)(uintptr_t)bp, j);
-      const int32_t v = test_point_warp(blob_view((const uint4*)(uintptr_t)pj), lj, px, py);
-      if (lane == j) id = v;
-    }
-    if (active) store(r, id);
-  }
+  for (uint32_t base = threadIdx.x & ~31u; base < count; base += blockDim.x)
+    test_warp_slice(ix, binned, first + base, min(32u, count - base), staged, region16, store);
 }
 
 }  // namespace pip

@@ -168,14 +168,8 @@ __global__ void __launch_bounds__(DQ_THREADS, 6) k_classify_dq(
 __global__ void k_scatter(const Residual* __restrict__ queue, const uint32_t* __restrict__ qcount,
                           const uint64_t* __restrict__ off, uint32_t* __restrict__ cursor,
                           Residual* __restrict__ binned) {
-  const uint32_t n = *qcount;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const Residual e = queue[i];
-    if (e.w == RES_HOLE) continue;
-    const uint32_t sb = e.w >> SB_LOG2;
-    const uint32_t pos = (uint32_t)off[sb] + atomicAdd(cursor + sb, 1u);
-    binned[pos] = e;
-  }
+  scatter_by_superbin(queue, *qcount, off, cursor, binned, blockIdx.x * blockDim.x + threadIdx.x,
+                      gridDim.x * blockDim.x);
 }
 
 // ------------------------------------------------------------------- K3
