@@ -144,7 +144,7 @@ def kernel_source_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2005_03156_gb300", "csrc")
     for f in sorted(os.listdir(d)):
-        if f in ("kernels.cuh", "pip_internal.cuh", "project.cu"):
+        if f in ("kernels.cuh", "pip_internal.cuh", "project.cu", "index.cu"):
             with open(os.path.join(d, f), "rb") as fh:
                 h.update(fh.read())
     return h.hexdigest()[:16]

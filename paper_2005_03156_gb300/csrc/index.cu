@@ -774,7 +774,7 @@ static void resolve_opts(const pip_build_opts& in, int64_t n_poly, long long w, 
   else if (o.max_depth < 0) o.max_depth = 0;  // uniform grid
   o.max_depth = std::min(o.max_depth, std::max(0, (o.cell_log2 - 1) / o.fanout_log2));
   if (o.leaf_edges <= 0) o.leaf_edges = 8;
-  if (o.size_ratio == 0) o.size_ratio = 16;
+  if (o.size_ratio == 0) o.size_ratio = 48;  // measured: deeper tries pay once K1 walks levels in bulk
   if (o.pts_per_cta <= 0) o.pts_per_cta = 256;
   if (o.stage_depth == 0) o.stage_depth = -1;  // measured best when chunks span many superbins
   if (o.stage_depth < 0) o.stage_depth = -1;  // no shared-memory staging

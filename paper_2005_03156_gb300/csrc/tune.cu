@@ -58,8 +58,8 @@ extern "C" pip_status pip_set_tune(pip_set set, const double* lon, const double*
   // 1) index shape: top cell size, subdivision ratio, leaf size
   const int s0 = start.cell_log2;
   for (int dc = -1; dc <= 1; ++dc)
-    for (int ratio : {8, 16, 24})
-      for (int le : {8, 24}) {
+    for (int ratio : {16, 32, 48, 64})
+      for (int le : {4, 8}) {
         pip_build_opts o = start;
         o.cell_log2 = std::max(4, std::min(30, s0 + dc));
         o.size_ratio = ratio;
