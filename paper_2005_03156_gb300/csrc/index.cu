@@ -1245,6 +1245,17 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
   v.nodes = S->nodes.p;
   v.blobs = S->blobs.p;
   v.sbdesc = S->sbdesc.p;
+  {  // L2-resident part of the trie: the top grid plus the first nodes (the
+     // shallow levels come first) up to three quarters of the L2
+    int dev = 0, l2 = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) != cudaSuccess || l2 <= 0) {
+      cudaGetLastError();
+      l2 = 64 << 20;
+    }
+    const int64_t budget = (int64_t)l2 * 3 / 4 - top_cells * 4;
+    v.hot_nodes = (uint32_t)std::max<int64_t>(0, std::min<int64_t>(n_nodes, budget / 32));
+  }
 
   pip_set_info_t& I = S->info;
   I.n_poly = S->n_poly;

@@ -258,9 +258,10 @@ struct TrieRing {
     count -= take;
     __syncwarp();  // every entry is read before the pushes below reuse slots
     NodeWords nw[4];
+    const uint64_t cold = policy_evict_first();
 #pragma unroll
     for (int j = 0; j < 4; ++j)
-      if ((have >> j) & 1u) nw[j] = ld_node(ix.nodes, d[j], pol);
+      if ((have >> j) & 1u) nw[j] = ld_node(ix.nodes, d[j], d[j] < ix.hot_nodes ? pol : cold);
     uint32_t leaf = 0, again = 0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {

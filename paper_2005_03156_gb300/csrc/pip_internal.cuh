@@ -68,7 +68,7 @@ struct IndexView {
   int32_t s0;             // log2 side of a top cell
   int32_t depth;          // deepest level present
   uint32_t n_sb;          // superbins
-  uint32_t pad;
+  uint32_t hot_nodes;     // nodes [0, hot_nodes) (the shallow levels) are kept in L2
   const uint32_t* table;  // top-grid descriptors
   const uint4* nodes;     // trie nodes, two uint4 per node
   const uint4* blobs;     // superbin records (16-byte units)
@@ -80,6 +80,15 @@ struct IndexView {
 __device__ __forceinline__ uint64_t policy_evict_last() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// Policy for the deep trie levels: each node there serves few points, so it
+// should not displace the top grid and the shallow levels, which every point
+// or most points read.
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
 

@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_classify_points(
 constexpr int DQ_THREADS = 128;
 
 template <bool VEC>
-__global__ void __launch_bounds__(DQ_THREADS, 6) k_classify_dq(
+__global__ void __launch_bounds__(DQ_THREADS, 5) k_classify_dq(
     IndexView ix, const double* __restrict__ lon, const double* __restrict__ lat, int64_t n,
     int32_t* __restrict__ out, Residual* __restrict__ queue, uint32_t* __restrict__ qcount,
     uint32_t* __restrict__ hist) {
