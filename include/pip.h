@@ -88,6 +88,14 @@ typedef struct {
   int32_t stage_depth;  /* shared-memory stages in the crossing kernel: 1 or 2, or
                            negative for none (records read through L1/L2); 0 = auto */
   int32_t cand_mode;    /* 0 = auto, 1 = descend the box hierarchy, 2 = rasterize block boxes */
+  int32_t approx_units; /* 0 = exact. > 0: error-bounded approximate mode (Sec. IV): boundary
+                           cells are split until their side is at most approx_units lattice
+                           units (max_depth is raised as needed), and each such leaf answers
+                           every point in it with the exact id of the leaf's centre lattice
+                           point, computed at build time, so no crossing test runs at query
+                           time. A returned id is then the exact id of a lattice point at
+                           Chebyshev distance <= approx_units / 2 of the query point. Leaves
+                           whose children overflow a trie node's palette stay exact. */
 } pip_build_opts;
 
 /* Facts about a loaded set's index (for tests, tuning and reports). */

@@ -32,7 +32,7 @@
 #include <cstring>
 #include <vector>
 
-#include "pip_internal.cuh"
+#include "kernels.cuh"
 
 namespace pip {
 
@@ -408,7 +408,7 @@ __global__ void k_classify(int64_t n_cell, const uint64_t* __restrict__ fc_coff,
                            uint32_t* __restrict__ desc, uint32_t* __restrict__ fc_nk,
                            uint32_t* __restrict__ fc_ne, uint32_t* __restrict__ fc_leaf,
                            uint32_t* __restrict__ fc_split, int32_t* __restrict__ fc_val, int shift,
-                           int can_split, uint32_t leaf_edges, int size_ratio,
+                           int can_split, uint32_t leaf_edges, int size_ratio, long long approx,
                            unsigned long long* counters) {
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cell;
        c += (int64_t)gridDim.x * blockDim.x) {
@@ -451,7 +451,8 @@ __global__ void k_classify(int64_t n_cell, const uint64_t* __restrict__ fc_coff,
       ne = 0;
     } else {
       const long long side = 1ll << shift;
-      const bool want = ne > leaf_edges || (size_ratio > 0 && side * size_ratio > min_ext);
+      const bool want = ne > leaf_edges || (size_ratio > 0 && side * size_ratio > min_ext) ||
+                        (approx > 0 && side > approx);
       if (can_split && want) {
         split = 1;
       } else {
@@ -757,6 +758,34 @@ pip_status d2h(T* h, const T* d, size_t n, cudaStream_t s) {
 
 }  // namespace
 
+// Approximate mode: the centre lattice point of each leaf cell of a level,
+// by leaf slot (slots past the level's leaves are padding with no candidates).
+__global__ void k_leaf_centers(int64_t n_leaf, const uint32_t* __restrict__ leaf_cell,
+                               const uint32_t* __restrict__ fc_x, const uint32_t* __restrict__ fc_y,
+                               Grid g, int shift, int2* __restrict__ centre) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_leaf;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t c = leaf_cell[i];
+    long long x0, y0, x1, y1;
+    cell_rect(g, shift, fc_x[c], fc_y[c], x0, y0, x1, y1);
+    const long long h = (1ll << shift) >> 1;
+    centre[i] = make_int2((int32_t)(x0 + h), (int32_t)(y0 + h));
+  }
+}
+
+// Approximate mode: the exact id of each leaf's centre, from the leaf's own
+// record (its kept edges decide every point of the cell, Sec. III-A test).
+__global__ void k_leaf_answer(int64_t n_slots, const int2* __restrict__ centre,
+                              const uint4* __restrict__ blobs, const uint2* __restrict__ sbdesc,
+                              int32_t* __restrict__ answer) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_slots;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int2 p = centre[t];
+    const BlobView b = blob_view(blobs + sbdesc[t >> SB_LOG2].x);
+    answer[t] = test_point(b, (uint32_t)(t & (SB_SLOTS - 1)), p.x, p.y);  // padding slots: no candidates, -1
+  }
+}
+
 // Resolve automatic options for a set.
 static void resolve_opts(const pip_build_opts& in, int64_t n_poly, long long w, long long h,
                          pip_build_opts& o, int n_levels) {
@@ -770,9 +799,16 @@ static void resolve_opts(const pip_build_opts& in, int64_t n_poly, long long w, 
     o.cell_log2 = std::max(4, std::min(30, s));
   }
   o.fanout_log2 = NODE_K;  // trie nodes hold 4 x 4 children
+  if (o.approx_units < 0) o.approx_units = 0;
+  if (o.approx_units == 1) o.approx_units = 2;  // the finest cells are 1 or 2 units wide
   if (o.max_depth == 0) o.max_depth = std::max(0, std::min(8, (o.cell_log2 - 6) / o.fanout_log2));
   else if (o.max_depth < 0) o.max_depth = 0;  // uniform grid
-  o.max_depth = std::min(o.max_depth, std::max(0, (o.cell_log2 - 1) / o.fanout_log2));
+  if (o.approx_units > 0) {  // leaves no wider than approx_units: enough levels for that
+    int need = 0;
+    while ((1ll << std::max(0, o.cell_log2 - o.fanout_log2 * need)) > o.approx_units) ++need;
+    o.max_depth = std::max(o.max_depth, need);
+  }
+  o.max_depth = std::min(o.max_depth, std::max(0, (o.cell_log2 - (o.approx_units > 0 ? 0 : 1)) / o.fanout_log2));
   if (o.leaf_edges <= 0) o.leaf_edges = 8;
   if (o.size_ratio == 0) o.size_ratio = 48;  // measured: deeper tries pay once K1 walks levels in bulk
   if (o.pts_per_cta <= 0) o.pts_per_cta = 256;
@@ -931,6 +967,7 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
   std::vector<int64_t> desc_len;
   std::vector<DBuf<uint4>> blob_lv;
   std::vector<DBuf<uint2>> sbd_lv;
+  std::vector<DBuf<int2>> cen_lv;  // approximate mode: leaf centres per level
   std::vector<int64_t> blob_len, sb_len;
   std::vector<DBuf<TrieNode>> node_lv;  // nodes of each level's split cells
   std::vector<int64_t> node_len;
@@ -1012,7 +1049,8 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
                                                  cd_keep.p, S->poly_box.p, fslot.p,
                                                  lv == 0 ? desc_lv[0].p : nullptr, fnk.p, fne.p, fleaf.p,
                                                  fsplit.p, fval.p, shift, can_split ? 1 : 0,
-                                                 (uint32_t)o.leaf_edges, o.size_ratio, counters);
+                                                 (uint32_t)o.leaf_edges, o.size_ratio,
+                                                 (long long)o.approx_units, counters);
     PIP_CUDA(cudaGetLastError());
     const int64_t n_parent = lv == 0 ? 0 : n_cell / fan;
     if (lv > 0) {  // palettes of the parents' nodes (may turn children into leaves)
@@ -1117,6 +1155,14 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
       std::vector<uint64_t> hs(n_sb);
       CHECK(d2h(hs.data(), bsize.p, n_sb, s));
       for (uint64_t v : hs) max_blob16 = std::max<int64_t>(max_blob16, (int64_t)v);
+      if (o.approx_units > 0) {
+        cen_lv.emplace_back();
+        ALLOC(cen_lv.back(), n_sb * SB_SLOTS);
+        PIP_CUDA(cudaMemsetAsync(cen_lv.back().p, 0, n_sb * SB_SLOTS * sizeof(int2), s));
+        k_leaf_centers<<<blocks_for(n_leaf), TB, 0, s>>>(n_leaf, leaf_cell.p, fx.p, fy.p, g, shift,
+                                                         cen_lv.back().p);
+        PIP_CUDA(cudaGetLastError());
+      }
       blob_len.push_back((int64_t)total16);
       sb_len.push_back(n_sb);
       blob_total16 += (int64_t)total16;
@@ -1222,6 +1268,21 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
       at_sb += sb_len[i];
     }
   }
+  S->approx.release();
+  if (o.approx_units > 0 && sb_total > 0) {  // approximate mode: answer of every leaf slot
+    const int64_t n_slots = sb_total * SB_SLOTS;
+    DBuf<int2> cen;
+    ALLOC(cen, n_slots);
+    int64_t at = 0;
+    for (size_t i = 0; i < cen_lv.size(); ++i) {
+      PIP_CUDA(cudaMemcpyAsync(cen.p + at, cen_lv[i].p, sb_len[i] * SB_SLOTS * sizeof(int2),
+                               cudaMemcpyDeviceToDevice, s));
+      at += sb_len[i] * SB_SLOTS;
+    }
+    if (!S->approx.alloc(al, (size_t)n_slots, s)) return fail(PIP_ENOMEM, "index: approximate answers");
+    k_leaf_answer<<<blocks_for(n_slots), TB, 0, s>>>(n_slots, cen.p, S->blobs.p, S->sbdesc.p, S->approx.p);
+    PIP_CUDA(cudaGetLastError());
+  }
   uint32_t e2 = 0;
   CHECK(d2h(&e2, err.p, 1, s));
   unsigned long long hc[3];
@@ -1245,6 +1306,7 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
   v.nodes = S->nodes.p;
   v.blobs = S->blobs.p;
   v.sbdesc = S->sbdesc.p;
+  v.approx_id = S->approx.p;  // nullptr unless approximate
   {  // L2-resident part of the trie: the top grid plus the first nodes (the
      // shallow levels come first) up to three quarters of the L2
     int dev = 0, l2 = 0;

@@ -271,7 +271,11 @@ struct TrieRing {
         d[j] = node_step(nw[j], sub);
         const uint32_t tag = d[j] >> 30;
         if (tag == TAG_INTERIOR) out_base[z[j]] = (int32_t)(d[j] & PAYLOAD_MASK);
-        leaf |= (tag == TAG_LEAF ? 1u : 0u) << j;
+        if (tag == TAG_LEAF && ix.approx_id) {  // approximate mode: the leaf's own answer
+          out_base[z[j]] = ix.approx_id[d[j] & PAYLOAD_MASK];
+        } else {
+          leaf |= (tag == TAG_LEAF ? 1u : 0u) << j;
+        }
         again |= (tag == TAG_CHILD ? 1u : 0u) << j;
         sh[j] -= NODE_K;
       }
@@ -316,7 +320,8 @@ __device__ __forceinline__ uint32_t classify4(const IndexView& ix, const double 
   for (int j = 0; j < 4; ++j) {
     const uint32_t tag = d[j] >> 30;
     id[j] = tag == TAG_INTERIOR ? (int32_t)(d[j] & PAYLOAD_MASK) : -1;
-    mask |= (tag == TAG_LEAF ? 1u : 0u) << j;
+    if (tag == TAG_LEAF && ix.approx_id) id[j] = ix.approx_id[d[j] & PAYLOAD_MASK];  // approximate mode
+    else mask |= (tag == TAG_LEAF ? 1u : 0u) << j;
   }
   return mask;
 }

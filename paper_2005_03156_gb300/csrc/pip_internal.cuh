@@ -73,6 +73,7 @@ struct IndexView {
   const uint4* nodes;     // trie nodes, two uint4 per node
   const uint4* blobs;     // superbin records (16-byte units)
   const uint2* sbdesc;    // per superbin: (offset, size) in 16-byte units
+  const int32_t* approx_id;  // approximate mode: id per leaf slot (nullptr when exact)
 };
 
 // L2 eviction policy for the index: keep it resident while the point stream
@@ -337,6 +338,7 @@ struct pip_set_s {
   pip::DBuf<uint4> nodes;
   pip::DBuf<uint4> blobs;
   pip::DBuf<uint2> sbdesc;
+  pip::DBuf<int32_t> approx;  // approximate mode: id per leaf slot
   pip::IndexView view{};
   pip_set_info_t info{};
   // error word for bounded device waits

@@ -142,7 +142,8 @@ __global__ void __launch_bounds__(DQ_THREADS, 5) k_classify_dq(
     for (int j = 0; j < 4; ++j) {
       const uint32_t tag = d[j] >> 30;
       id[j] = tag == TAG_INTERIOR ? (int32_t)(d[j] & PAYLOAD_MASK) : -1;
-      leaf |= (tag == TAG_LEAF ? 1u : 0u) << j;
+      if (tag == TAG_LEAF && ix.approx_id) id[j] = ix.approx_id[d[j] & PAYLOAD_MASK];  // approximate mode
+      else leaf |= (tag == TAG_LEAF ? 1u : 0u) << j;
       split |= (tag == TAG_CHILD ? 1u : 0u) << j;
     }
     if (VEC && i0 + 3 < n) {

@@ -117,3 +117,17 @@ def test_two_gloo_ranks_shard_and_reduce():
         for a, b, ids in parts:
             got[a:b] = ids
         assert (got == want).all()
+
+
+def _struct_fields(name):
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r";", text)
+    assert m, name
+    return re.findall(r"\b(?:int32_t|int64_t|double|void\s*\*|pip_set|const double\s*\*|int32_t\s*\*)\s+([a-z_0-9]+)\s*;", m.group(1))
+
+
+def test_binding_structs_match_the_header():
+    from paper_2005_03156_gb300 import _native
+    for cname, pycls in (("pip_build_opts", _native.BuildOpts), ("pip_project_stats", _native.ProjectStats)):
+        assert _struct_fields(cname) == [f for f, _ in pycls._fields_], cname

@@ -279,3 +279,49 @@ def test_parent_ids_follow_the_hierarchy(pipm, tiny_set):
         assert (got == want).all(), level
     with pytest.raises(pipm.PipError):
         pipm.pip_parent_ids(s, ids, len(tiny_set.parents) + 1)
+
+
+@pytest.mark.parametrize("case", ["tiny_4096", "small_64"])
+def test_approximate_mode_error_bound(pipm, tiny_set, case):
+    """Approximate mode (Sec. IV, the error-bounded variant of true-hit
+    filtering): no crossing test runs at query time; a point in a boundary
+    leaf (side 2^k <= approx_units, aligned to the top grid) gets the exact
+    id (oracle) of the leaf's centre lattice point, which lies at Chebyshev
+    distance <= approx_units / 2; every other point gets its exact id. The
+    check: each returned id equals the oracle's id at the point or at the
+    centre of one of the aligned power-of-two cells of side <= approx_units
+    around it."""
+    if case == "tiny_4096":
+        ps, approx = tiny_set, 4096
+    else:
+        ps, approx = configs.tiny_set(n_blocks=200, deg=0.1, origin=(0.3, 0.4)), 64
+    s = pipm.load_polygon_set(ps, opts={"approx_units": approx})
+    lon, lat = configs.tiny_points(ps, n=200_000, seed=11)
+    out, stats = pipm.pip_project_ex(s, dev(lon), dev(lat))
+    pipm.pip_set_check(s)
+    got = out.cpu().numpy()
+    assert stats["residual"] == 0  # every leaf answers from its table entry
+    want = oracle.join_hier(ps, lon, lat)
+    qx, ok_x = oracle.quantize(lon)
+    qy, ok_y = oracle.quantize(lat)
+    ok = ok_x & ok_y
+    assert (got[~ok] == -1).all()
+    info = s.info()
+    gx0, gy0 = int(info["grid_x0"]), int(info["grid_y0"])
+    allowed = got == want
+    k = 0
+    while (1 << k) <= approx:
+        side = 1 << k
+        cx = gx0 + ((qx.astype(np.int64) - gx0) // side) * side + side // 2
+        cy = gy0 + ((qy.astype(np.int64) - gy0) // side) * side + side // 2
+        assert (np.abs(cx - qx) <= approx // 2).all() and (np.abs(cy - qy) <= approx // 2).all()
+        at_centre = oracle.join_hier(ps, lattice_to_degrees(cx), lattice_to_degrees(cy))
+        allowed |= got == at_centre
+        k += 1
+    bad = np.nonzero(ok & ~allowed)[0]
+    assert len(bad) == 0, (len(bad), bad[:5].tolist())
+    mism = int((got != want).sum())
+    assert mism < 0.05 * len(got), mism
+    # the same set built exact still answers exactly
+    e = pipm.load_polygon_set(ps)
+    assert (project(pipm, e, lon, lat) == want).all()
