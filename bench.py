@@ -297,7 +297,8 @@ def run_ours(args):
     k3 = float(np.mean(prof["k3_ms"])) if len(prof["k3_ms"]) else float("nan")
     peak, peak_kind = measured_peak()
     achieved = BYTES_PER_POINT * n / (k1 / 1e3) / 1e9
-    traffic = recorded_traffic(n)
+    # the recorded traffic is for the default index of the state workload
+    traffic = recorded_traffic(n) if (not opts and args.config == "state") else None
 
     e2e = None
     if not args.no_e2e:
@@ -331,7 +332,7 @@ def run_ours(args):
                        "index": {k: info[k] for k in ("cell_log2", "fanout_log2", "depth", "leaves",
                                                       "interior_cells", "superbins", "index_bytes",
                                                       "build_ms", "table_entries")},
-                       "residual_fraction": pstats["residual"] / n},
+                       "residual_fraction": pstats["residual"] / n, "build_opts": opts or "default"},
             "roofline": {"bound": "hbm", "kernel": "k_classify_dq (K1)", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json copy bandwidth)",
@@ -587,6 +588,20 @@ def run_national(args):
         pipm.pip_project(s, lon_h, lat_h, out_h)
     dt = (time.perf_counter() - t) / steps
     clk = clocks.stop()
+    # device-resident time of one chunk, by stage (what the stream hides behind the copies)
+    dl = lon_h[:chunk].cuda()
+    da = lat_h[:chunk].cuda()
+    do = torch.empty(chunk, dtype=torch.int32, device="cuda")
+    pipm.pip_project(s, dl, da, do)
+    pipm.pip_profile_enable(s, 3)
+    for _ in range(3):
+        pipm.pip_project(s, dl, da, do)
+    torch.cuda.synchronize()
+    prof = pipm.pip_profile_read(s, 3)
+    pipm.pip_profile_enable(s, 0)
+    chunk_stages = {"k1_classify": float(np.mean(prof["k1_ms"])), "k2_bin": float(np.mean(prof["bin_ms"])),
+                    "k3_cross": float(np.mean(prof["k3_ms"]))}
+    del dl, da, do
     n = n_chunks * chunk
     idx = np.random.default_rng(5).choice(n, 100_000, replace=False)
     import oracle
@@ -602,7 +617,7 @@ def run_national(args):
                    "index": {k: s.info()[k] for k in ("cell_log2", "depth", "leaves", "index_bytes", "build_ms")},
                    "generation_s": {"set": gen_set, "points": gen_pts}},
         "h2d_gbs": h2d_gbs, "bound_pts_s": bound, "frac_of_bound": (n / dt) / bound,
-        "sampled_parity_100k": ok, "clocks": clk,
+        "sampled_parity_100k": ok, "clocks": clk, "device_chunk_stages_ms": chunk_stages,
     }
     print(json.dumps(line))
 

@@ -214,6 +214,15 @@ pip_status pip_project_noalloc(pip_set set, const double* lon, const double* lat
 pip_status pip_parent_ids(pip_set set, const int32_t* ids, int64_t n, int32_t level, int32_t* out,
                           void* stream);
 
+/* Diagnostic of the failure path of bounded device waits: launches one CTA
+ * that waits on an mbarrier nothing completes, giving up after limit_ns
+ * (0 < limit_ns <= 1e10) nanoseconds of %globaltimer, as every wait in the
+ * library does after 2 s. Returns PIP_ETIMEOUT when the wait ran out (the
+ * expected outcome; the context stays usable), PIP_OK if it completed,
+ * PIP_EINVAL for a bad limit, PIP_ECUDA on a CUDA error. Synchronises
+ * `stream`. The paper has no counterpart. */
+pip_status pip_selftest_bounded_wait(int64_t limit_ns, void* stream);
+
 /* Device error word of the set (a bounded device wait that ran out sets it):
  * synchronises `stream`, returns PIP_OK or PIP_ETIMEOUT and clears it. */
 pip_status pip_set_check(pip_set set, void* stream);

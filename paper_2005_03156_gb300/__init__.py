@@ -81,7 +81,7 @@ class PolygonSet:
             pass
 
 
-def _load(fn, vx, vy, ring_off, poly_ring_off, parents, opts, stream):
+def _load(fn, vx, vy, ring_off, poly_ring_off, parents, opts, stream, allocator=None):
     ring_off = np.ascontiguousarray(ring_off, np.int64) if isinstance(ring_off, np.ndarray) else ring_off
     poly_ring_off = (np.ascontiguousarray(poly_ring_off, np.int64)
                      if isinstance(poly_ring_off, np.ndarray) else poly_ring_off)
@@ -91,18 +91,23 @@ def _load(fn, vx, vy, ring_off, poly_ring_off, parents, opts, stream):
     handle = ctypes.c_void_p(0)
     o = _opts(opts)
     st = fn(_ptr(vx), _ptr(vy), int(len(vx)), _ptr(ring_off), int(len(ring_off) - 1), _ptr(poly_ring_off),
-            int(len(poly_ring_off) - 1), par_arr, len(parents), ctypes.byref(o) if o else None, None,
-            _stream(stream), ctypes.byref(handle))
+            int(len(poly_ring_off) - 1), par_arr, len(parents), ctypes.byref(o) if o else None,
+            ctypes.byref(allocator) if allocator is not None else None, _stream(stream),
+            ctypes.byref(handle))
     _native.check(st)
-    return PolygonSet(handle.value)
+    ps = PolygonSet(handle.value)
+    ps._allocator = allocator  # the set calls it until freed
+    return ps
 
 
-def pip_set_load_i32(vx, vy, ring_off, poly_ring_off, parents=None, opts=None, stream=None) -> PolygonSet:
-    """Load int32 lattice vertices (numpy host arrays or torch tensors)."""
+def pip_set_load_i32(vx, vy, ring_off, poly_ring_off, parents=None, opts=None, stream=None,
+                     allocator=None) -> PolygonSet:
+    """Load int32 lattice vertices (numpy host arrays or torch tensors).
+    allocator: optional _native.Allocator (device memory hook)."""
     if isinstance(vx, np.ndarray):
         vx = np.ascontiguousarray(vx, np.int32)
         vy = np.ascontiguousarray(vy, np.int32)
-    return _load(lib().pip_set_load_i32, vx, vy, ring_off, poly_ring_off, parents, opts, stream)
+    return _load(lib().pip_set_load_i32, vx, vy, ring_off, poly_ring_off, parents, opts, stream, allocator)
 
 
 def pip_set_load_f64(vx, vy, ring_off, poly_ring_off, parents=None, opts=None, stream=None) -> PolygonSet:
@@ -113,10 +118,11 @@ def pip_set_load_f64(vx, vy, ring_off, poly_ring_off, parents=None, opts=None, s
     return _load(lib().pip_set_load_f64, vx, vy, ring_off, poly_ring_off, parents, opts, stream)
 
 
-def load_polygon_set(pset, opts=None, stream=None) -> PolygonSet:
+def load_polygon_set(pset, opts=None, stream=None, allocator=None) -> PolygonSet:
     """Load a synth.PolygonSet-like object (vx, vy, ring_off, poly_ring_off, parents)."""
     return pip_set_load_i32(pset.vx, pset.vy, pset.ring_off, pset.poly_ring_off,
-                            parents=getattr(pset, "parents", None), opts=opts, stream=stream)
+                            parents=getattr(pset, "parents", None), opts=opts, stream=stream,
+                            allocator=allocator)
 
 
 def pip_set_info(s: PolygonSet) -> dict:
@@ -193,6 +199,12 @@ def pip_quantize(v, stream=None):
     ok = torch.empty(v.shape[0], dtype=torch.uint8, device=v.device)
     _native.check(lib().pip_quantize(_ptr(v), int(v.shape[0]), _ptr(q), _ptr(ok), _stream(stream)))
     return q, ok
+
+
+def pip_selftest_bounded_wait(limit_ns: int, stream=None) -> int:
+    """Run the bounded-wait failure path once (diagnostic): returns the
+    status code, PIP_ETIMEOUT (5) when the wait ran out as designed."""
+    return int(lib().pip_selftest_bounded_wait(int(limit_ns), _stream(stream)))
 
 
 def pip_set_top_candidates(s: PolygonSet, mode: int):

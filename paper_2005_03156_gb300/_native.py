@@ -92,6 +92,7 @@ SIGNATURES = {
     "pip_server_stats": (I32, [P, P, I32]),
     "pip_server_destroy": (None, [P]),
     "pip_quantize": (I32, [P, I64, P, P, P]),
+    "pip_selftest_bounded_wait": (I32, [I64, P]),
     "pip_set_top_candidates": (I32, [P, I32, P, P, I64]),
     "pip_profile_enable": (I32, [P, I32]),
     "pip_profile_read": (I32, [P, P, P, P, P]),

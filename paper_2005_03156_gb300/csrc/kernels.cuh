@@ -2,11 +2,13 @@
 // forms.
 //
 //   K1 classify   streams the points (two 16-byte loads of lon and two of lat
-//                 per 4 points), quantizes them with integer instructions,
-//                 walks the cell trie and writes the id of points in EMPTY
-//                 and INTERIOR cells at once (Sec. IV true-hit filtering).
-//                 Points in boundary leaves are appended to a residual queue
-//                 (warp-aggregated atomics) and counted per superbin.
+//                 per 4 points), quantizes them with integer instructions and
+//                 reads their top-grid descriptors; EMPTY and INTERIOR cells
+//                 answer at once (Sec. IV true-hit filtering). Points in split
+//                 cells wait in a per-warp ring (TrieRing) that is walked one
+//                 trie level for 128 points at a time. Points in boundary
+//                 leaves go to the residual queue through per-warp chunks
+//                 (ChunkWriter) and are counted per superbin.
 //   K2 bin        counting sort of the residual by superbin: scan of the
 //                 counts and a scatter, so points that share polygons sit
 //                 together (the GPU form of sorting the points so many share
@@ -356,7 +358,8 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
 }
 
 // Bounded wait for phase `parity` of bar; false when it ran out.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          unsigned long long limit_ns = WAIT_NS) {
   const uint32_t a = smem_addr(bar);
   uint32_t done = 0;
   asm volatile(
@@ -373,7 +376,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
-    if (global_ns() - t0 > WAIT_NS) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
 }
 

@@ -289,6 +289,19 @@ __global__ void __launch_bounds__(K3_THREADS) k_cross_direct(IndexView ix,
   }
 }
 
+// Failure path of the bounded waits: one CTA waits on an mbarrier that
+// nothing completes; the wait gives up after limit_ns, the kernel records
+// the outcome (1 = ran out, 2 = completed) and returns.
+__global__ void k_bounded_wait_probe(uint32_t* __restrict__ outcome, unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *outcome = mbar_wait(&bar, 0u, limit_ns) ? 2u : 1u;
+}
+
 // ------------------------------------------------------------------- host
 static void init_pool_once() {
   static std::once_flag f[64];
@@ -569,4 +582,23 @@ extern "C" pip_status pip_project_ex(pip_set set, const double* lon, const doubl
 extern "C" pip_status pip_project(pip_set set, const double* lon, const double* lat, int64_t n,
                                   int32_t* out, void* stream) {
   return pip_project_ex(set, lon, lat, n, out, stream, nullptr);
+}
+
+extern "C" pip_status pip_selftest_bounded_wait(int64_t limit_ns, void* stream) {
+  if (limit_ns <= 0 || limit_ns > 10ll * 1000 * 1000 * 1000)
+    return fail(PIP_EINVAL, "pip_selftest_bounded_wait: 0 < limit_ns <= 1e10");
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t* d = nullptr;
+  PIP_CUDA(cudaMallocAsync((void**)&d, sizeof(uint32_t), s));
+  PIP_CUDA(cudaMemsetAsync(d, 0, sizeof(uint32_t), s));
+  k_bounded_wait_probe<<<1, 32, 0, s>>>(d, (unsigned long long)limit_ns);
+  cudaError_t e = cudaGetLastError();
+  uint32_t h = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFreeAsync(d, s);
+  if (e != cudaSuccess) return cuda_fail(e, "pip_selftest_bounded_wait");
+  count_launches(1);
+  if (h == 1u) return fail(PIP_ETIMEOUT, "pip_selftest_bounded_wait: the wait ran out (expected)");
+  return h == 2u ? PIP_OK : fail(PIP_ECUDA, "pip_selftest_bounded_wait: no outcome recorded");
 }

@@ -325,3 +325,66 @@ def test_approximate_mode_error_bound(pipm, tiny_set, case):
     # the same set built exact still answers exactly
     e = pipm.load_polygon_set(ps)
     assert (project(pipm, e, lon, lat) == want).all()
+
+
+def test_bounded_wait_runs_out_and_context_survives(pipm, tiny_set):
+    """Failure detection without a fault: a device wait on an mbarrier that
+    nothing completes gives up after its limit, the kernel reports it
+    (PIP_ETIMEOUT) and returns, and the context keeps working."""
+    import time
+    t0 = time.perf_counter()
+    assert pipm.pip_selftest_bounded_wait(20_000_000) == 5  # 20 ms limit -> PIP_ETIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    with pytest.raises(pipm.PipError):
+        pipm._native.check(pipm.pip_selftest_bounded_wait(0))
+    s = pipm.load_polygon_set(tiny_set)
+    lon, lat = configs.tiny_points(tiny_set, n=50_000)
+    assert (project(pipm, s, lon, lat) == oracle.join_hier(tiny_set, lon, lat)).all()
+
+
+def _torch_allocator(fail_after=None):
+    """An allocator hook on torch's caching allocator that records live
+    blocks; with fail_after=k the (k+1)-th allocation returns NULL."""
+    from paper_2005_03156_gb300 import _native
+    state = {"live": {}, "allocs": 0, "frees": 0}
+
+    @_native.ALLOC_FN
+    def alloc(nbytes, stream, ctx):
+        if fail_after is not None and state["allocs"] >= fail_after:
+            return None
+        state["allocs"] += 1
+        p = torch.cuda.caching_allocator_alloc(max(int(nbytes), 1))
+        state["live"][p] = int(nbytes)
+        return p
+
+    @_native.FREE_FN
+    def free(ptr, stream, ctx):
+        state["frees"] += 1
+        state["live"].pop(ptr)
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return _native.Allocator(alloc, free, None), state
+
+
+def test_allocator_hook_and_injected_failures(pipm, tiny_set):
+    """Every device allocation of a set goes through the caller's hook; an
+    allocation that fails part-way through a load gives PIP_ENOMEM and every
+    block taken so far is given back; the context keeps working."""
+    lon, lat = configs.tiny_points(tiny_set, n=30_000)
+    want = oracle.join_hier(tiny_set, lon, lat)
+    A, st = _torch_allocator()
+    s = pipm.load_polygon_set(tiny_set, allocator=A)
+    assert (project(pipm, s, lon, lat) == want).all()
+    assert st["allocs"] > 0
+    s.free()
+    torch.cuda.synchronize()
+    assert not st["live"] and st["frees"] == st["allocs"]
+    for k in (0, 1, 5, 20):
+        B, sb = _torch_allocator(fail_after=k)
+        with pytest.raises(pipm.PipError) as e:
+            pipm.load_polygon_set(tiny_set, allocator=B)
+        assert e.value.status == 2, (k, e.value)
+        torch.cuda.synchronize()
+        assert not sb["live"], (k, len(sb["live"]))
+    s2 = pipm.load_polygon_set(tiny_set)
+    assert (project(pipm, s2, lon, lat) == want).all()
