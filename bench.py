@@ -579,7 +579,8 @@ def run_national(args):
         best = min(best, time.perf_counter() - t)
     h2d_gbs = chunk * 8 / best / 1e9
     del dbuf
-    pipm.pip_project(s, lon_h, lat_h, out_h)  # warm: touches every pinned page once
+    for _ in range(max(1, args.warmup)):  # warm: touches every pinned page; early host-to-device
+        pipm.pip_project(s, lon_h, lat_h, out_h)  # copies after a large index build ran slower
     clocks = ClockSampler(0)
     clocks.start()
     t = time.perf_counter()
@@ -610,7 +611,7 @@ def run_national(args):
     bound = min(6773.2, h2d_gbs) * 1e9 / 16
     line = {
         "metric": METRIC + " (national, streamed from pinned host)", "value": n / dt, "unit": UNIT,
-        "n_gpus": 1, "steps": steps, "warmup": 1, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "n_gpus": 1, "steps": steps, "warmup": max(1, args.warmup), "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": f"national: {ps.n_poly} blocks in 50 regions, {n:.0e} points in "
                                f"{n_chunks} chunks of 1e8 from pinned host memory",
