@@ -132,6 +132,42 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+_ALL_CPUS = None  # the process's CPUs before bind_host_to_gpu
+
+
+def bind_host_to_gpu(device: int):
+    """Run this process on the CPUs next to the GPU (its PCI device's
+    local_cpulist), so pinned host buffers are first touched in the GPU's
+    NUMA node and host-to-device copies do not cross sockets. Returns the
+    CPU list used, or None when it cannot be determined."""
+    try:
+        import torch
+        p = torch.cuda.get_device_properties(device)
+        bus = getattr(p, "pci_bus_id", None)
+        dom = getattr(p, "pci_domain_id", 0) or 0
+        dev = getattr(p, "pci_device_id", 0) or 0
+        if bus is None:
+            return None
+        path = f"/sys/bus/pci/devices/{dom:04x}:{bus:02x}:{dev:02x}.0/local_cpulist"
+        spec = open(path).read().strip()
+        cpus = set()
+        for part in spec.split(","):
+            if "-" in part:
+                a, b = part.split("-")
+                cpus.update(range(int(a), int(b) + 1))
+            elif part:
+                cpus.add(int(part))
+        global _ALL_CPUS
+        _ALL_CPUS = os.sched_getaffinity(0)
+        cpus &= _ALL_CPUS
+        if not cpus:
+            return None
+        os.sched_setaffinity(0, cpus)
+        return spec
+    except Exception:
+        return None
+
+
 def measured_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -178,6 +214,8 @@ def cpu_baseline(ps, lon, lat, budget_s=12.0):
     sample of the same points (sized for ~budget_s seconds)."""
     import numpy as np
     import oracle
+    if _ALL_CPUS:
+        os.sched_setaffinity(0, _ALL_CPUS)  # the oracle gets every host core
     cores = os.cpu_count() or 1
     H = oracle.Hier(ps, threads=cores)  # hierarchy prepared once, outside the timing
     t = time.perf_counter()
@@ -239,6 +277,7 @@ def run_ours(args):
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
+    host_cpus = bind_host_to_gpu(local)
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -326,7 +365,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": {"workload": desc, "points_per_gpu": n, "polygons": ps.n_poly,
+            "config": {"host_cpus": host_cpus, "workload": desc, "points_per_gpu": n, "polygons": ps.n_poly,
                        "vertices": ps.n_vert, "l2": "inputs larger than L2 (1.6 GB of points per step vs 129 MB L2)",
                        "parallelism": f"replicas x{ws} (points sharded, set replicated)",
                        "index": {k: info[k] for k in ("cell_log2", "fanout_log2", "depth", "leaves",
@@ -365,6 +404,7 @@ def run_batched(args):
     pbuild.build()
     import paper_2005_03156_gb300 as pipm
     torch.cuda.set_device(0)
+    host_cpus = bind_host_to_gpu(0)
     t0 = time.perf_counter()
     psets = configs.batched_sets()
     sizes, sigma = configs.batched_query_sizes()
@@ -434,7 +474,7 @@ def run_batched(args):
         "metric": METRIC + " (batched)", "value": n_total / (batched_ms / 1e3), "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": batched_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": f"batched: {len(qs)} queries (lognormal, sigma {sigma:.2f}, 100..1e6, mean "
+        "config": {"host_cpus": host_cpus, "workload": f"batched: {len(qs)} queries (lognormal, sigma {sigma:.2f}, 100..1e6, mean "
                                f"{sizes.mean():.0f}) over 8 sets of {min(p.n_poly for p in psets)}.."
                                f"{max(p.n_poly for p in psets)} blocks, {n_total} points",
                    "plan": knobs, "generation_s": gen_s, "tuned_sets": bool(args.tune)},
@@ -457,6 +497,7 @@ def run_serve(args):
     pbuild.build()
     import paper_2005_03156_gb300 as pipm
     torch.cuda.set_device(0)
+    host_cpus = bind_host_to_gpu(0)
     seeds = (configs.SEEDS["state"], 6, 7)
     psets = [configs.state_set(seed=sd) for sd in seeds]
     sets = [pipm.load_polygon_set(p) for p in psets]
@@ -526,7 +567,7 @@ def run_serve(args):
         "metric": "p50/p99 serve latency and sustained " + METRIC, "value": best["served"]["sustained_pts_s"],
         "unit": UNIT, "n_gpus": 1, "steps": len(loads), "warmup": 0, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": "serving: Poisson arrivals, sizes log-uniform [1, 1e6], 3 resident "
+        "config": {"host_cpus": host_cpus, "workload": "serving: Poisson arrivals, sizes log-uniform [1, 1e6], 3 resident "
                                "state-scale sets (seeds 2, 6, 7), pinned host buffers",
                    "requests_per_load": args.requests},
         "loads": results,
@@ -549,6 +590,7 @@ def run_national(args):
     pbuild.build()
     import paper_2005_03156_gb300 as pipm
     torch.cuda.set_device(0)
+    host_cpus = bind_host_to_gpu(0)
     t0 = time.perf_counter()
     ps = configs.national_set()
     s = pipm.load_polygon_set(ps, opts=_opts_arg(args))
@@ -613,7 +655,7 @@ def run_national(args):
         "metric": METRIC + " (national, streamed from pinned host)", "value": n / dt, "unit": UNIT,
         "n_gpus": 1, "steps": steps, "warmup": max(1, args.warmup), "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": f"national: {ps.n_poly} blocks in 50 regions, {n:.0e} points in "
+        "config": {"host_cpus": host_cpus, "workload": f"national: {ps.n_poly} blocks in 50 regions, {n:.0e} points in "
                                f"{n_chunks} chunks of 1e8 from pinned host memory",
                    "index": {k: s.info()[k] for k in ("cell_log2", "depth", "leaves", "index_bytes", "build_ms")},
                    "generation_s": {"set": gen_set, "points": gen_pts}},
