@@ -244,14 +244,14 @@ def run_reference(args):
     oracle.build()
     ps, lon, lat, n, desc = workload(args.config, 0, args.points)
     cores = os.cpu_count() or 1
-    sample = 4_000_000
+    sample = min(4_000_000, n)  # points per step: a bounded sample of the workload
     H = oracle.Hier(ps, threads=cores)  # the oracle's box hierarchy, prepared once
     for i in range(args.warmup):
-        a = (i * sample) % max(1, n - sample)
+        a = (i * sample) % max(1, n - sample + 1)
         H.join(lon[a:a + sample], lat[a:a + sample])
     times = []
     for i in range(args.steps):
-        a = ((args.warmup + i) * sample) % max(1, n - sample)
+        a = ((args.warmup + i) * sample) % max(1, n - sample + 1)
         t = time.perf_counter()
         H.join(lon[a:a + sample], lat[a:a + sample])
         times.append(time.perf_counter() - t)
