@@ -229,27 +229,6 @@ __device__ __forceinline__ uint32_t edge_crosses(int4 e, int32_t px, int32_t py)
   return (uint32_t)(in_y & (right | (span & (l > r))));
 }
 
-// Trie lookup: descriptor of the leaf cell holding (qx, qy). Returns
-// TAG_EMPTY for points outside the grid.
-__device__ __forceinline__ uint32_t lookup(const IndexView& ix, int32_t qx, int32_t qy) {
-  const uint32_t dx = (uint32_t)qx - (uint32_t)ix.gx0;
-  const uint32_t dy = (uint32_t)qy - (uint32_t)ix.gy0;
-  const uint32_t cx = dx >> ix.s0, cy = dy >> ix.s0;
-  if (cx >= ix.nx || cy >= ix.ny || qx < ix.gx0 || qy < ix.gy0) return make_desc(TAG_EMPTY, 0);
-  const uint64_t pol = policy_evict_last();
-  uint32_t d = ld_index_u32(ix.table + (size_t)cy * ix.nx + cx, pol);
-  int s = ix.s0;
-  const uint32_t m = (1u << NODE_K) - 1u;
-#pragma unroll 1
-  while ((d >> 30) == TAG_CHILD) {
-    s -= NODE_K;
-    const uint32_t node = d & PAYLOAD_MASK;
-    const uint32_t sub = (((dy >> s) & m) << NODE_K) | ((dx >> s) & m);
-    d = node_step(ld_node(ix.nodes, node, pol), sub);
-  }
-  return d;
-}
-
 // ---------------------------------------------------------------------------
 // Host-side helpers
 // ---------------------------------------------------------------------------

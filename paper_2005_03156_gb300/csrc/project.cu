@@ -1,6 +1,7 @@
 // The plain projection path: K1 classify -> K2 bin -> K3 cross on one
 // stream, plus the chunked host-memory pipeline.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 
@@ -326,10 +327,12 @@ static pip_status k3_launch(const IndexView& ix, int stages, const Residual* bin
                             const uint32_t* qcount, uint32_t ppc, uint32_t* item_ctr,
                             int32_t* out, uint32_t* status, cudaStream_t s) {
   if (stages < 0) {
-    static int occ = 0;
+    static std::atomic<int> occ_cache{0};  // same on every device of one architecture
+    int occ = occ_cache.load(std::memory_order_relaxed);
     if (!occ) {
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cross_direct, K3_THREADS, 0);
       occ = std::max(1, occ);
+      occ_cache.store(occ, std::memory_order_relaxed);
     }
     const unsigned grid = (unsigned)(num_sms() * occ);
     k_cross_direct<<<grid, K3_THREADS, 0, s>>>(ix, binned, qcount, ppc, item_ctr, out);
@@ -338,13 +341,16 @@ static pip_status k3_launch(const IndexView& ix, int stages, const Residual* bin
   }
   uint32_t stage_bytes = 0;
   const int smem = k3_smem_config(stages, stage_bytes);
-  static bool attr_set[3] = {false, false, false};
-  if (!attr_set[stages]) {
+  static std::atomic<uint32_t> attr_set[64];  // per device: bit `stages` once the attribute is set
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!(attr_set[dev].load(std::memory_order_acquire) & (1u << stages))) {
     if (stages == 2)
       PIP_CUDA(cudaFuncSetAttribute(k_cross<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     else
       PIP_CUDA(cudaFuncSetAttribute(k_cross<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    attr_set[stages] = true;
+    attr_set[dev].fetch_or(1u << stages, std::memory_order_acq_rel);
   }
   const int ctas_per_sm = std::max(1, (int)((200 * 1024) / (smem + 2048)));
   const unsigned grid = (unsigned)(num_sms() * std::min(ctas_per_sm, 4));
@@ -366,11 +372,13 @@ pip_status k3_launch_public(const IndexView& ix, int stages, const Residual* bin
 
 // K1 grid: one persistent wave of the deferred-queue kernel.
 static unsigned k1_grid(int64_t n) {
-  static int occ = 0;
+  static std::atomic<int> occ_cache{0};
+  int occ = occ_cache.load(std::memory_order_relaxed);
   if (!occ) {
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_classify_dq<true>, DQ_THREADS, 0) != cudaSuccess)
       occ = 1;
     occ = std::max(1, occ);
+    occ_cache.store(occ, std::memory_order_relaxed);
   }
   const int64_t groups = (n + 3) / 4;
   return (unsigned)std::max<int64_t>(
@@ -402,11 +410,13 @@ cudaError_t k1_launch(const IndexView& ix, const double* lon, const double* lat,
 cudaError_t k1_launch_lockstep(const IndexView& ix, const double* lon, const double* lat, int64_t n,
                                int32_t* out, Residual* queue, uint32_t* qcount, uint32_t* hist,
                                cudaStream_t s) {
-  static int occ = 0;
+  static std::atomic<int> occ_cache{0};
+  int occ = occ_cache.load(std::memory_order_relaxed);
   if (!occ) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_classify_points<true>, K1_THREADS, 0);
     if (e != cudaSuccess) return e;
     occ = std::max(1, occ);
+    occ_cache.store(occ, std::memory_order_relaxed);
   }
   const bool vec = ((uintptr_t)lon % 16 == 0) && ((uintptr_t)lat % 16 == 0) && ((uintptr_t)out % 16 == 0);
   const int64_t groups = (n + 3) / 4;
