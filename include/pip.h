@@ -292,7 +292,8 @@ pip_status pip_server_submit(pip_server srv, int32_t set, const double* lon, con
                              int64_t n, int32_t* out, uint64_t* ticket);
 /* Wait up to timeout_us (< 0 = forever) for a ticket. PIP_ETIMEOUT if not done. */
 pip_status pip_server_wait(pip_server srv, uint64_t ticket, int64_t timeout_us);
-/* Latency percentiles of completed requests since creation or the last reset. */
+/* Latency percentiles of completed requests since creation or the last reset
+ * (over the most recent 4,194,304 completions when there were more). */
 pip_status pip_server_stats(pip_server srv, pip_server_stats_t* st, int32_t reset);
 void pip_server_destroy(pip_server srv);
 

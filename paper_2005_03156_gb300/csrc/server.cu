@@ -29,6 +29,7 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 constexpr int64_t GATHER_MAX = 1 << 15;  // requests up to this size are gathered on the CPU
+constexpr int64_t LAT_WINDOW = 1 << 22;  // latency samples kept for the percentiles
 
 struct Req {
   uint64_t ticket = 0;
@@ -63,7 +64,8 @@ struct pip_server_s {
   std::vector<std::unique_ptr<Slot>> slots;
   std::thread dispatcher;
   // stats
-  std::vector<double> lat_us;
+  std::vector<double> lat_us;  // latencies of the most recent LAT_WINDOW completions (a ring)
+  int64_t lat_seen = 0;        // completions recorded since the last reset
   int64_t submitted = 0, completed = 0, rejected = 0, launches = 0, points = 0, batch_queries = 0;
 };
 
@@ -103,7 +105,10 @@ void CUDART_CB slot_done(void* arg) {
     if (r->gathered && r->n > 0) std::memcpy(r->out, sl->hout + r->off, r->n * sizeof(int32_t));
     r->t_done = now;
     r->state = 2;
-    S->lat_us.push_back(std::chrono::duration<double, std::micro>(r->t_done - r->t_sub).count());
+    const double us = std::chrono::duration<double, std::micro>(r->t_done - r->t_sub).count();
+    if ((int64_t)S->lat_us.size() < LAT_WINDOW) S->lat_us.push_back(us);
+    else S->lat_us[S->lat_seen % LAT_WINDOW] = us;
+    ++S->lat_seen;
     ++S->completed;
   }
   sl->batch.clear();
@@ -323,6 +328,7 @@ extern "C" pip_status pip_server_stats(pip_server srv, pip_server_stats_t* st, i
   }
   if (reset) {
     srv->lat_us.clear();
+    srv->lat_seen = 0;
     srv->submitted = srv->completed = srv->rejected = srv->launches = srv->points = 0;
     srv->batch_queries = 0;
   }
