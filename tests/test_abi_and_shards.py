@@ -131,3 +131,47 @@ def test_binding_structs_match_the_header():
     from paper_2005_03156_gb300 import _native
     for cname, pycls in (("pip_build_opts", _native.BuildOpts), ("pip_project_stats", _native.ProjectStats)):
         assert _struct_fields(cname) == [f for f, _ in pycls._fields_], cname
+
+
+def _failing_rank_main(rank, world, port, q):
+    import datetime
+
+    import torch.distributed as dist
+
+    from paper_2005_03156_gb300.shard import max_over_ranks
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    if rank == 1:
+        os._exit(3)  # this rank dies between steps, before the step's timing reduction
+    try:
+        max_over_ranks(1.0)
+        q.put((rank, "no error"))
+    except Exception as e:  # the survivor's collective must fail, not hang
+        q.put((rank, type(e).__name__))
+
+
+def test_dead_rank_fails_the_timing_reduction_instead_of_hanging():
+    import multiprocessing as mp
+    import queue
+    import time
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_failing_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    t0 = time.time()
+    for p in procs:
+        p.start()
+    try:
+        rank, what = q.get(timeout=120)
+    except queue.Empty:
+        rank, what = None, "hung"
+    for p in procs:
+        p.join(timeout=30)
+        if p.is_alive():
+            p.kill()
+            p.join()
+    assert rank == 0 and what not in ("no error", "hung"), (rank, what)
+    assert procs[1].exitcode == 3
+    assert time.time() - t0 < 150
