@@ -388,3 +388,17 @@ def test_allocator_hook_and_injected_failures(pipm, tiny_set):
         assert not sb["live"], (k, len(sb["live"]))
     s2 = pipm.load_polygon_set(tiny_set)
     assert (project(pipm, s2, lon, lat) == want).all()
+
+
+def test_too_many_points_for_one_device_call_is_refused(pipm, tiny_set):
+    """The residual queue is indexed with 32 bits: a device-resident call of
+    2^32 points is refused with PIP_EINVAL before any memory is touched."""
+    import ctypes
+    s = pipm.load_polygon_set(tiny_set)
+    lon, lat = dev(np.zeros(4)), dev(np.zeros(4))
+    out = torch.empty(4, dtype=torch.int32, device="cuda")
+    lib = pipm._native.load()
+    st = lib.pip_project(s.handle, ctypes.c_void_p(lon.data_ptr()), ctypes.c_void_p(lat.data_ptr()),
+                         1 << 32, ctypes.c_void_p(out.data_ptr()), None)
+    assert st == 1  # PIP_EINVAL
+    assert (project(pipm, s, np.zeros(4), np.zeros(4)) == oracle.join_hier(tiny_set, np.zeros(4), np.zeros(4))).all()
