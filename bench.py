@@ -53,6 +53,7 @@ def parse():
                          "pinned host memory")
     ap.add_argument("--tune", action="store_true", help="run the autotuner on a sample first")
     ap.add_argument("--requests", type=int, default=20000, help="serve: requests per offered load")
+    ap.add_argument("--queries", type=int, default=0, help="batched: use only the first N queries")
     ap.add_argument("--loads", default="1e8,2e8,5e8,1e9", help="serve: offered loads in points/s")
     return ap.parse_args()
 
@@ -408,9 +409,11 @@ def run_batched(args):
     t0 = time.perf_counter()
     psets = configs.batched_sets()
     sizes, sigma = configs.batched_query_sizes()
-    n_total = int(sizes.sum())
     rng = np.random.Generator(np.random.PCG64([configs.SEEDS["batched"], 600]))
     set_of = rng.integers(0, len(psets), len(sizes))
+    if args.queries:  # the first queries only (small cases for profiling)
+        sizes, set_of = sizes[:args.queries], set_of[:args.queries]
+    n_total = int(sizes.sum())
     sets = [pipm.load_polygon_set(p) for p in psets]
     # points: each set's mixture, one block of points per set, queries slice it
     per_set = [int(sizes[set_of == k].sum()) + 2 * int((set_of == k).sum()) for k in range(len(psets))]
