@@ -1,7 +1,7 @@
 """Plain CPU oracle for the point-in-polygon join (test infrastructure only).
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline
-leg may import this package. The product library never loads it, and the two
+leg and reference arm may import this package. The product library never loads it, and the two
 share no code.
 
 The oracle follows the paper (Kepner et al., "Fast Mapping onto Census

@@ -2,7 +2,8 @@
 //
 // TEST INFRASTRUCTURE ONLY. Nothing on the product path may call, link or
 // load this file; only tests/, __graft_entry__.smoke() and bench.py's CPU
-// baseline leg use it. It shares no source with the CUDA library.
+// baseline leg and reference arm use it. It shares no source with the CUDA
+// library.
 //
 // What it computes (Kepner et al., "Fast Mapping onto Census Blocks"):
 //   * Sec. II: points are IEEE doubles (x_pt = longitude, y_pt = latitude);
