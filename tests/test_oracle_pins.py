@@ -150,6 +150,14 @@ MUTANTS = {
                           "return x_min < px && px < x_max && y_min < py && py < y_max;"),
     "highest_index_claims": ("std::sort(cand.begin(), cand.end());",
                              "std::sort(cand.rbegin(), cand.rend());"),
+    "parity_or": ("parity ^= edge_crossing(s.vx[i], s.vy[i], s.vx[j], s.vy[j], px, py);",
+                  "parity |= edge_crossing(s.vx[i], s.vy[i], s.vx[j], s.vy[j], px, py);"),
+    "transposed_orientation": ("const i128 s = (i128)(bx - ax) * (py - ay) - (i128)(by - ay) * (px - ax);",
+                               "const i128 s = (i128)(bx - ax) * (px - ax) - (i128)(by - ay) * (py - ay);"),
+    "q_truncates": ("if (rest > half || (rest == half && (whole & 1))) whole += 1;",
+                    "(void)rest;"),
+    "last_vertex_skipped": ("for (int64_t i = first; i <= last; ++i) {",
+                            "for (int64_t i = first; i < last; ++i) {"),
 }
 
 
