@@ -259,9 +259,12 @@ pip_status pip_plan_tune(pip_plan plan, const pip_query* q, int32_t n_q, void* s
 /* One-shot convenience: create a plan, run, destroy (synchronous). */
 pip_status pip_project_batch(const pip_query* q, int32_t n_q, void* stream);
 
-/* Autotuner: time candidate (cell_log2, pts_per_cta, stage_depth) settings
- * on a sample of the set's queries (device pointers) and rebuild the set
- * with the fastest; the chosen options are written to *chosen (may be NULL). */
+/* Autotuner: time candidate index shapes (cell_log2 - 1 .. + 1, split ratio
+ * 16 / 32 / 48 / 64, 4 or 8 kept edges per leaf) and then crossing work items
+ * (pts_per_cta 128 .. 1024, stage_depth none / 1 / 2) on a sample of the
+ * set's queries (device pointers), and rebuild the set with the fastest; the
+ * chosen options are written to *chosen (may be NULL). Synchronous. Shapes
+ * whose index fails to build (too large) are skipped. */
 pip_status pip_set_tune(pip_set set, const double* lon, const double* lat, int64_t n_sample,
                         void* stream, pip_build_opts* chosen);
 
