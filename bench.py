@@ -11,8 +11,16 @@ One step = one pip_project call over the whole batch (K1 classify + K2 bin +
 K3 cross), inputs resident in HBM. Under torchrun (N > 1) every rank
 projects its own 1e8 points against a replica of the set (weak scaling, no
 collective on the data path); value = all ranks' points / max rank time.
+At N = 1 the same line also carries the metric's two other parts, measured
+after the plain join: "batched" (the 4,096-query batched workload over 8
+resident sets in one graph launch, against the same queries as separate
+plain launches) and "serve" (one offered load of the serving workload over
+3 resident state-scale sets: p50/p99 latency of the continuous-batching
+server against per-request plain launches); --no-batched / --no-serve skip
+them. The polygon sets are built in spawned worker processes meanwhile.
 --impl reference times the CPU oracle (hierarchical box filter + exact
 crossing test, all host cores) on bounded samples of the same workload.
+Other modes: --mode batched | serve | national (one workload each).
 """
 from __future__ import annotations
 
@@ -55,6 +63,10 @@ def parse():
     ap.add_argument("--requests", type=int, default=20000, help="serve: requests per offered load")
     ap.add_argument("--queries", type=int, default=0, help="batched: use only the first N queries")
     ap.add_argument("--loads", default="1e8,2e8,5e8,1e9", help="serve: offered loads in points/s")
+    ap.add_argument("--no-batched", action="store_true", help="plain mode: skip the batched leg")
+    ap.add_argument("--no-serve", action="store_true", help="plain mode: skip the serving leg")
+    ap.add_argument("--serve-load", type=float, default=5e8, help="plain mode: the serving leg's offered load")
+    ap.add_argument("--serve-requests", type=int, default=3000, help="plain mode: the serving leg's requests")
     return ap.parse_args()
 
 
@@ -65,7 +77,7 @@ def dist_env():
     return ws, rank, local
 
 
-def workload(cfg, rank, n_override):
+def workload(cfg, rank, n_override, ps=None):
     from synth import configs
     if cfg == "tiny":
         ps = configs.tiny_set()
@@ -73,7 +85,7 @@ def workload(cfg, rank, n_override):
         lon, lat = configs.tiny_points(ps, n=n, seed=configs.SEEDS["tiny"] + rank)
         desc = f"tiny plain join: {ps.n_poly} Voronoi blocks over 1x1 deg, {n:.0e} uniform lattice points (+1% outside)"
     else:
-        ps = configs.state_set()
+        ps = ps if ps is not None else configs.state_set()
         n = n_override or 100_000_000
         lon, lat = configs.state_points(n=n, stream=1 + rank)
         desc = (f"state-scale plain join: {ps.n_poly} blocks (40 counties, ~5,000 tracts) over 5x5 deg, "
@@ -187,26 +199,22 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+TRAFFIC_JSON = os.path.join(ROOT, "profiles", "k1_classify_state.json")
+
+
 def recorded_traffic(points):
-    """DRAM bytes per K1 launch from the committed ncu summary, scaled to
-    `points`, if it was taken on the current kernel sources; else None."""
-    path = os.path.join(ROOT, "profiles", "k1_classify_state.md")
+    """DRAM bytes (read + write) per K1 launch from the committed summary of
+    one ncu capture of K1 on the state workload, scaled to `points` (the
+    bytes per point do not depend on the point count: one pass over the
+    points against the same index), when the capture was taken on the
+    current kernel sources; else None."""
     try:
-        txt = open(path).read()
-    except OSError:
-        return None
-    vals = {}
-    for line in txt.splitlines():
-        if line.startswith("<!--") and "=" in line:
-            for kv in line.strip("<!-> ").split():
-                if "=" in kv:
-                    k, v = kv.split("=", 1)
-                    vals[k] = v
-    if vals.get("source_hash") != kernel_source_hash():
-        return None
-    try:
-        return float(vals["dram_bytes_per_point"]) * points
-    except (KeyError, ValueError):
+        with open(TRAFFIC_JSON) as f:
+            rec = json.load(f)
+        if rec.get("source_hash") != kernel_source_hash():
+            return None
+        return float(rec["dram_bytes_per_point"]) * points
+    except (OSError, KeyError, ValueError):
         return None
 
 
@@ -277,6 +285,14 @@ def run_ours(args):
     import torch
 
     ws, rank, local = dist_env()
+    # the batched and serving legs run at N=1 on the default workload; their
+    # polygon sets are built in worker processes while this one works
+    legs = ws == 1 and args.config == "state" and not args.points
+    do_batched, do_serve = legs and not args.no_batched, legs and not args.no_serve
+    jobs = [("state", SERVE_SEEDS[0])] if ws == 1 and args.config == "state" else []
+    jobs += [("state", sd) for sd in SERVE_SEEDS[1:]] if do_serve else []
+    jobs += BATCHED_JOBS if do_batched else []
+    ex, futs = start_generation(jobs) if jobs else (None, {})
     torch.cuda.set_device(local)
     host_cpus = bind_host_to_gpu(local)
     if ws > 1:
@@ -286,7 +302,8 @@ def run_ours(args):
     pbuild.build()
     import paper_2005_03156_gb300 as pipm
 
-    ps, lon, lat, n, desc = workload(args.config, rank, args.points)
+    pre = futs[("state", SERVE_SEEDS[0])].result() if ("state", SERVE_SEEDS[0]) in futs else None
+    ps, lon, lat, n, desc = workload(args.config, rank, args.points, ps=pre)
     opts = {}
     for kv in filter(None, args.opts.split(",")):
         k, v = kv.split("=")
@@ -361,6 +378,23 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(ps, lon, lat)
 
+    # the batched and serving legs (the metric's other two parts), on the
+    # same GPU after the plain join's buffers are released
+    batched = serve = None
+    if do_batched or do_serve:
+        del dlon, dlat, out
+        s.free()
+        torch.cuda.empty_cache()
+    if do_batched:
+        bsets = [futs[j].result() for j in BATCHED_JOBS]
+        batched = batched_leg(pipm, bsets, steps=5, warmup=2)
+        del bsets
+    if do_serve:
+        ssets = [ps] + [futs[("state", sd)].result() for sd in SERVE_SEEDS[1:]]
+        serve = serve_leg(pipm, ssets, [args.serve_load], args.serve_requests)
+    if ex is not None:
+        ex.shutdown()
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -376,10 +410,22 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "kernel": "k_classify_dq (K1)", "achieved": achieved,
                          "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                          "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json copy bandwidth)",
-                         "bytes_per_launch": BYTES_PER_POINT * n},
+                         "bytes_per_launch": BYTES_PER_POINT * n,
+                         "step": {"achieved": BYTES_PER_POINT * n / (ms_step / 1e3) / 1e9,
+                                  "frac": BYTES_PER_POINT * n / (ms_step / 1e3) / 1e9 / peak,
+                                  "note": "the whole projection (K1 + K2 + K3) against the same 20 B/point"}},
             "stages_ms": {"k1_classify": k1, "k2_bin": bn, "k3_cross": k3},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
         }
+        if batched is not None:
+            line["batched"] = batched
+            line["config"]["batched"] = batched["workload"] + ", 5 timed graph launches after 2 warm-up"
+        if serve is not None:
+            r = serve["loads"][0]
+            line["serve"] = {"offered_pts_s": r["served"]["offered_pts_s"], "requests": args.serve_requests,
+                             "served": r["served"], "plain_per_request": r["plain_per_request"],
+                             "served_equals_plain": r["served_equals_plain"], "clocks": serve["clocks"]}
+            line["config"]["serve"] = serve["workload"]
         print(json.dumps(line))
     if ws > 1:
         import torch.distributed as dist
@@ -394,27 +440,43 @@ def _opts_arg(args):
     return opts or None
 
 
-def run_batched(args):
-    """4096 lognormal queries (100..1e6 points, mean ~5e4) over 8 resident
-    sets of 10k..200k blocks: one persistent graph launch per step against
-    4096 separate plain launches of the same queries."""
+def _gen_set(kind, arg):
+    """One polygon set, built in a worker process (picklable result)."""
+    from synth import configs
+    if kind == "state":
+        return configs.state_set(seed=arg)
+    return configs.batched_set(arg)
+
+
+def start_generation(jobs):
+    """Build polygon sets in spawned worker processes, started before any
+    CUDA call (spawn, not fork: the workers hold no CUDA state)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    ex = cf.ProcessPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 1)),
+                                mp_context=mp.get_context("spawn"))
+    return ex, {job: ex.submit(_gen_set, *job) for job in jobs}
+
+
+BATCHED_JOBS = [("batched", k) for k in range(8)]
+SERVE_SEEDS = (2, 6, 7)  # the state seed and two more: 3 resident state-scale sets
+
+
+def batched_leg(pipm, psets, steps, warmup, opts=None, n_queries=0, tune=False):
+    """4096 lognormal queries (100..1e6 points, mean ~5e4) over the 8
+    resident sets: one persistent graph launch per step against the same
+    queries as separate plain launches (3 rounds)."""
     import numpy as np
     import torch
     from synth import configs
-    from paper_2005_03156_gb300 import build as pbuild
-    pbuild.build()
-    import paper_2005_03156_gb300 as pipm
-    torch.cuda.set_device(0)
-    host_cpus = bind_host_to_gpu(0)
     t0 = time.perf_counter()
-    psets = configs.batched_sets()
     sizes, sigma = configs.batched_query_sizes()
     rng = np.random.Generator(np.random.PCG64([configs.SEEDS["batched"], 600]))
     set_of = rng.integers(0, len(psets), len(sizes))
-    if args.queries:  # the first queries only (small cases for profiling)
-        sizes, set_of = sizes[:args.queries], set_of[:args.queries]
+    if n_queries:  # the first queries only (small cases for profiling)
+        sizes, set_of = sizes[:n_queries], set_of[:n_queries]
     n_total = int(sizes.sum())
-    sets = [pipm.load_polygon_set(p) for p in psets]
+    sets = [pipm.load_polygon_set(p, opts=opts) for p in psets]
     # points: each set's mixture, one block of points per set, queries slice it
     per_set = [int(sizes[set_of == k].sum()) + 2 * int((set_of == k).sum()) for k in range(len(psets))]
     pts = []
@@ -423,7 +485,7 @@ def run_batched(args):
                                                     np.random.Generator(np.random.PCG64([configs.SEEDS["batched"], 700 + k])))
         pts.append((torch.from_numpy(lon).cuda(), torch.from_numpy(lat).cuda()))
     gen_s = time.perf_counter() - t0
-    if args.tune:
+    if tune:
         for k, s in enumerate(sets):
             m = min(5_000_000, per_set[k])
             if m > 0:
@@ -440,7 +502,7 @@ def run_batched(args):
         outs.append(out)
     plan = pipm.Plan(max_points=n_total, max_queries=len(qs))
     knobs = plan.tune(qs)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         plan.run(qs)
     plan.check()
     stream = torch.cuda.current_stream()
@@ -449,20 +511,20 @@ def run_batched(args):
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         plan.run(qs)
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    batched_ms = e0.elapsed_time(e1) / args.steps
-    batched_launches = (pipm.pip_kernel_launches() - l0) / args.steps
+    batched_ms = e0.elapsed_time(e1) / steps
+    batched_launches = (pipm.pip_kernel_launches() - l0) / steps
     plan.check()
     got = [o.clone() for o in outs]
     # the same queries as separate plain launches
     for q in qs[:64]:
         pipm.pip_project(q[0], q[1], q[2], q[3])
     torch.cuda.synchronize()
-    plain_steps = max(1, min(3, args.steps))
+    plain_steps = max(1, min(3, steps))
     l0 = pipm.pip_kernel_launches()
     e0.record(stream)
     for _ in range(plain_steps):
@@ -473,53 +535,73 @@ def run_batched(args):
     plain_ms = e0.elapsed_time(e1) / plain_steps
     plain_launches = (pipm.pip_kernel_launches() - l0) / plain_steps
     equal = all(torch.equal(a, b) for a, b in zip(got, outs))
-    line = {
-        "metric": METRIC + " (batched)", "value": n_total / (batched_ms / 1e3), "unit": UNIT, "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": batched_ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"host_cpus": host_cpus, "workload": f"batched: {len(qs)} queries (lognormal, sigma {sigma:.2f}, 100..1e6, mean "
-                               f"{sizes.mean():.0f}) over 8 sets of {min(p.n_poly for p in psets)}.."
-                               f"{max(p.n_poly for p in psets)} blocks, {n_total} points",
-                   "plan": knobs, "generation_s": gen_s, "tuned_sets": bool(args.tune)},
+    for s in sets:
+        s.free()
+    del pts, qs, outs, got
+    torch.cuda.empty_cache()
+    return {
+        "value": n_total / (batched_ms / 1e3), "unit": UNIT, "ms_per_step": batched_ms, "steps": steps,
+        "warmup": warmup, "gpu_launches": batched_launches,
+        "workload": f"batched: {len(sizes)} queries (lognormal, sigma {sigma:.2f}, 100..1e6, mean "
+                    f"{sizes.mean():.0f}) over 8 sets of {min(p.n_poly for p in psets)}.."
+                    f"{max(p.n_poly for p in psets)} blocks, {n_total} points",
+        "points": n_total, "plan": knobs, "generation_s": gen_s, "tuned_sets": bool(tune),
         "plain_per_query": {"value": n_total / (plain_ms / 1e3), "ms_per_step": plain_ms,
-                            "gpu_launches": plain_launches},
-        "speedup_vs_plain": plain_ms / batched_ms, "batched_equals_plain": equal,
-        "gpu_launches": batched_launches, "clocks": clk,
+                            "gpu_launches": plain_launches, "rounds": plain_steps},
+        "speedup_vs_plain": plain_ms / batched_ms, "batched_equals_plain": equal, "clocks": clk,
     }
-    print(json.dumps(line))
 
 
-def run_serve(args):
-    """Poisson arrivals at each offered load, request sizes log-uniform in
-    [1, 1e6], uniform over 3 resident state-scale sets: the continuous-
-    batching server against per-request plain launches (pinned host buffers)."""
-    import numpy as np
+def run_batched(args):
+    """The batched workload alone (see batched_leg)."""
     import torch
-    from synth import configs
+    ex, futs = start_generation(BATCHED_JOBS)
     from paper_2005_03156_gb300 import build as pbuild
     pbuild.build()
     import paper_2005_03156_gb300 as pipm
     torch.cuda.set_device(0)
     host_cpus = bind_host_to_gpu(0)
-    seeds = (configs.SEEDS["state"], 6, 7)
-    psets = [configs.state_set(seed=sd) for sd in seeds]
+    psets = [futs[j].result() for j in BATCHED_JOBS]
+    ex.shutdown()
+    leg = batched_leg(pipm, psets, args.steps, args.warmup, opts=_opts_arg(args), n_queries=args.queries,
+                      tune=args.tune)
+    line = {
+        "metric": METRIC + " (batched)", "value": leg["value"], "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": leg["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"host_cpus": host_cpus, "workload": leg["workload"], "plan": leg["plan"],
+                   "generation_s": leg["generation_s"], "tuned_sets": leg["tuned_sets"]},
+        "plain_per_query": leg["plain_per_query"], "speedup_vs_plain": leg["speedup_vs_plain"],
+        "batched_equals_plain": leg["batched_equals_plain"], "gpu_launches": leg["gpu_launches"],
+        "clocks": leg["clocks"],
+    }
+    print(json.dumps(line))
+
+
+def serve_leg(pipm, psets, loads, nreq):
+    """Poisson arrivals at each offered load, request sizes log-uniform in
+    [1, 1e6], uniform over the resident state-scale sets: the continuous-
+    batching server against per-request plain launches (pinned host buffers)."""
+    import numpy as np
+    import torch
+    from synth import configs
     sets = [pipm.load_polygon_set(p) for p in psets]
     pool_n = 20_000_000
     pools = []
-    for sd in seeds:
+    for sd in SERVE_SEEDS[:len(psets)]:
         lon, lat = configs.state_points(n=pool_n, seed=sd, stream=9)
         pools.append((torch.from_numpy(lon).pin_memory(), torch.from_numpy(lat).pin_memory()))
-    loads = [float(x) for x in args.loads.split(",")]
     results = []
+    clocks = ClockSampler(0)
+    clocks.start()
     for load in loads:
         rng = np.random.Generator(np.random.PCG64([configs.SEEDS["serve"], int(load) % 100003]))
-        nreq = args.requests
         sizes = np.exp(rng.uniform(0, np.log(1e6), nreq)).astype(np.int64)
         sizes = np.maximum(1, sizes)
         mean = sizes.mean()
         gaps = rng.exponential(mean / load, nreq)
         arrive = np.cumsum(gaps)
-        which = rng.integers(0, 3, nreq)
+        which = rng.integers(0, len(sets), nreq)
         offs = rng.integers(0, pool_n - 1_000_000, nreq)
         outs = [torch.empty(int(n), dtype=torch.int32).pin_memory() for n in sizes]
 
@@ -547,9 +629,11 @@ def run_serve(args):
         wall = time.perf_counter() - t0
         st = srv.stats()
         srv.close()
+        served_ids = [o.clone() for o in outs]
         served = {"offered_pts_s": load, "p50_us": st["p50_us"], "p99_us": st["p99_us"],
                   "sustained_pts_s": float(sizes.sum()) / wall, "launches": st["launches"],
-                  "mean_batch_queries": st["mean_batch_queries"], "requests": nreq}
+                  "mean_batch_queries": st["mean_batch_queries"], "requests": nreq,
+                  "points": int(sizes.sum())}
         # per-request plain launches, in arrival order (a request starts when
         # it has arrived and the previous one is done)
         lat_us = np.zeros(nreq)
@@ -563,17 +647,39 @@ def run_serve(args):
         wall_p = time.perf_counter() - t0
         plain = {"p50_us": float(np.percentile(lat_us, 50)), "p99_us": float(np.percentile(lat_us, 99)),
                  "sustained_pts_s": float(sizes.sum()) / wall_p}
-        results.append({"served": served, "plain_per_request": plain})
+        equal = all(torch.equal(a, b) for a, b in zip(served_ids, outs))
+        results.append({"served": served, "plain_per_request": plain, "served_equals_plain": equal})
         print(json.dumps({"load": load, **results[-1]}), file=sys.stderr, flush=True)
-    best = max(results, key=lambda r: r["served"]["sustained_pts_s"])
+    clk = clocks.stop()
+    for s in sets:
+        s.free()
+    return {"loads": results, "clocks": clk,
+            "workload": f"serving: Poisson arrivals, sizes log-uniform [1, 1e6], {len(sets)} resident "
+                        f"state-scale sets (seeds {', '.join(str(x) for x in SERVE_SEEDS[:len(sets)])}), "
+                        f"pinned host buffers, {nreq} requests per offered load"}
+
+
+def run_serve(args):
+    """The serving workload alone (see serve_leg)."""
+    import torch
+    jobs = [("state", sd) for sd in SERVE_SEEDS]
+    ex, futs = start_generation(jobs)
+    from paper_2005_03156_gb300 import build as pbuild
+    pbuild.build()
+    import paper_2005_03156_gb300 as pipm
+    torch.cuda.set_device(0)
+    host_cpus = bind_host_to_gpu(0)
+    psets = [futs[j].result() for j in jobs]
+    ex.shutdown()
+    loads = [float(x) for x in args.loads.split(",")]
+    leg = serve_leg(pipm, psets, loads, args.requests)
+    best = max(leg["loads"], key=lambda r: r["served"]["sustained_pts_s"])
     line = {
         "metric": "p50/p99 serve latency and sustained " + METRIC, "value": best["served"]["sustained_pts_s"],
         "unit": UNIT, "n_gpus": 1, "steps": len(loads), "warmup": 0, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"host_cpus": host_cpus, "workload": "serving: Poisson arrivals, sizes log-uniform [1, 1e6], 3 resident "
-                               "state-scale sets (seeds 2, 6, 7), pinned host buffers",
-                   "requests_per_load": args.requests},
-        "loads": results,
+        "config": {"host_cpus": host_cpus, "workload": leg["workload"], "requests_per_load": args.requests},
+        "loads": leg["loads"], "clocks": leg["clocks"],
     }
     print(json.dumps(line))
 

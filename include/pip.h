@@ -96,6 +96,19 @@ typedef struct {
                            time. A returned id is then the exact id of a lattice point at
                            Chebyshev distance <= approx_units / 2 of the query point. Leaves
                            whose children overflow a trie node's palette stay exact. */
+  int32_t compact_edges; /* compact leaves: a boundary leaf whose kept candidates (at most 3)
+                           share at most this many distinct edges is answered in the classify
+                           kernel by the exact crossing test (Sec. III-A) on those edges, read
+                           from one 32..128-byte record, instead of going through the residual
+                           queue and crossing kernel. 1..7 = on with at most that many edges;
+                           0 = auto (off: on the state-scale workload the classify kernel's
+                           extra work cost more than the residual kernels it saves); negative
+                           = off. Always off in approximate mode and for sets of more than
+                           2^24 polygons. */
+  int32_t compact_early; /* 1: a boundary cell that fits a compact record stops splitting there
+                           (a shallower trie; the other boundary cells split to max_depth);
+                           0 = auto: the split rules above decide the trie's shape and compact
+                           records replace only its leaves. Ignored when compact_edges is off. */
 } pip_build_opts;
 
 /* Facts about a loaded set's index (for tests, tuning and reports). */
@@ -116,6 +129,9 @@ typedef struct {
   int32_t grid_x0, grid_y0; /* lattice origin of the grid */
   int64_t grid_nx, grid_ny;
   double build_ms;          /* device time of the last index build */
+  int64_t compact_leaves;   /* boundary cells answered from compact records */
+  int64_t compact_bytes;    /* bytes of those records (inside the trie-node array) */
+  int64_t compact_by_edges[8]; /* compact leaves by number of distinct edges 0..7 */
 } pip_set_info_t;
 
 /* Per-call counters of pip_project_ex (read after the stream is synchronised). */
@@ -201,7 +217,13 @@ pip_status pip_project_ex(pip_set set, const double* lon, const double* lat, int
  * call before any stream capture. All calls share the array and it keeps
  * the last call's contents (the call clears what must start at zero), so
  * calls that overlap on the GPU race: serialise them (one stream, or
- * synchronise between calls). Asynchronous on `stream`; results are the
+ * synchronise between calls). Unlike pip_project, which switches to the
+ * set's device itself, this call requires the set's device to be the
+ * current device (PIP_EINVAL otherwise), so that it never changes devices
+ * inside a capture. The looked-up address is kept for the life of the
+ * process: after cudaDeviceReset, or any teardown of the device's primary
+ * context, do not call it again in that process (the kept address would
+ * belong to the old context). Asynchronous on `stream`; results are the
  * same as pip_project's. */
 pip_status pip_project_noalloc(pip_set set, const double* lon, const double* lat, int64_t n,
                                int32_t* out, void* stream);
@@ -272,7 +294,8 @@ pip_status pip_set_tune(pip_set set, const double* lon, const double* lat, int64
 
 typedef struct {
   int32_t n_streams;          /* concurrent launches in flight (0 = 2) */
-  int64_t mem_budget_bytes;   /* device bytes for in-flight requests (0 = 1/4 of free) */
+  int64_t mem_budget_bytes;   /* device bytes reserved at creation for in-flight requests
+                                 (0 = 1/4 of the memory free at creation) */
   int64_t max_batch_points;   /* points coalesced into one launch (0 = 1<<24) */
   int32_t max_batch_queries;  /* requests coalesced into one launch (0 = 1024) */
   int32_t max_pending;        /* queued requests before submit says PIP_EBUSY (0 = 1<<20) */
@@ -287,10 +310,19 @@ typedef struct {
 /* Start a serving loop over resident sets (the sets must outlive it). */
 pip_status pip_server_create(const pip_set* sets, int32_t n_sets, const pip_server_opts* opts,
                              pip_server* out);
-/* Queue a request: lon/lat/out are host memory (pinned is fastest) that
- * stays valid until pip_server_wait reports it done. A request that arrives
- * while others run is admitted into the next launch as soon as a stream and
- * device memory are free (continuous batching). */
+/* Queue a request of any size n >= 0: lon/lat/out are host memory (pinned
+ * is fastest) that stays valid until pip_server_wait reports it done. The
+ * device memory for requests in flight is reserved once, at
+ * pip_server_create, from mem_budget_bytes (default: a quarter of the memory
+ * free at that moment) and split into n_streams slots of equal point
+ * capacity; admission is then against a free slot and its capacity, not
+ * against memory free at run time. A request that arrives while others run
+ * joins the next launch whose slot frees up (continuous batching). A request
+ * larger than one slot is queued as consecutive parts of at most a slot each
+ * and its ticket completes when the last part is done; its results equal a
+ * single pip_project call. PIP_EBUSY when the queue (in parts) would exceed
+ * max_pending; PIP_EINVAL for a bad set, NULL buffers with n > 0 or a
+ * stopping server. */
 pip_status pip_server_submit(pip_server srv, int32_t set, const double* lon, const double* lat,
                              int64_t n, int32_t* out, uint64_t* ticket);
 /* Wait up to timeout_us (< 0 = forever) for a ticket. PIP_ETIMEOUT if not done. */
@@ -322,6 +354,19 @@ pip_status pip_set_top_candidates(pip_set set, int32_t cand_mode, int64_t* off, 
  * array of length *n; *n is updated to the number returned. */
 pip_status pip_profile_enable(pip_set set, int32_t capacity);
 pip_status pip_profile_read(pip_set set, double* k1_ms, double* bin_ms, double* k3_ms, int32_t* n);
+
+/* Which cell of the set's index answers each lattice point: code[i] for
+ * the point (qx[i], qy[i]) (device pointers, asynchronous) is a kind in bits
+ * 0-7 and the trie depth of the answering cell in bits 8-15 (0 = a top-grid
+ * cell). Kinds: EMPTY and INTERIOR cells answer without a crossing test
+ * (Sec. IV, true-hit filtering); COMPACT leaves answer with the test inside
+ * the classify kernel; RESIDUAL leaves send the point to the crossing
+ * kernel; OUTSIDE = beyond the grid (answered -1). For tests and tuning:
+ * the projection never calls it. */
+enum { PIP_LOC_EMPTY = 0, PIP_LOC_INTERIOR = 1, PIP_LOC_RESIDUAL = 2, PIP_LOC_COMPACT = 3,
+       PIP_LOC_OUTSIDE = 4 };
+pip_status pip_locate(pip_set set, const int32_t* qx, const int32_t* qy, int64_t n, uint32_t* code,
+                      void* stream);
 
 /* Kernel launches the library has issued in this process so far. */
 int64_t pip_kernel_launches(void);

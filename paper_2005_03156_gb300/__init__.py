@@ -25,7 +25,7 @@ __all__ = [
     "PipError", "BuildOpts", "PolygonSet", "pip_set_load_i32", "pip_set_load_f64", "pip_project",
     "pip_project_ex", "pip_quantize", "pip_set_info", "pip_set_rebuild", "pip_set_free",
     "pip_set_check", "pip_set_top_candidates", "pip_project_batch", "Plan", "pip_set_tune",
-    "Server", "lib",
+    "Server", "lib", "pip_locate",
 ]
 
 
@@ -128,7 +128,21 @@ def load_polygon_set(pset, opts=None, stream=None, allocator=None) -> PolygonSet
 def pip_set_info(s: PolygonSet) -> dict:
     info = SetInfo()
     _native.check(lib().pip_set_info(s.handle, ctypes.byref(info)))
-    return {k: getattr(info, k) for k, _ in SetInfo._fields_}
+    d = {k: getattr(info, k) for k, _ in SetInfo._fields_}
+    d["compact_by_edges"] = list(d["compact_by_edges"])
+    return d
+
+
+LOC_KINDS = {0: "empty", 1: "interior", 2: "residual", 3: "compact", 4: "outside"}
+
+
+def pip_locate(s: PolygonSet, qx, qy, stream=None):
+    """Kind (bits 0-7) and trie depth (bits 8-15) of the index cell that
+    answers each lattice point (int32 device tensors); see LOC_KINDS."""
+    import torch
+    code = torch.empty(int(qx.shape[0]), dtype=torch.int32, device=qx.device)
+    _native.check(lib().pip_locate(s.handle, _ptr(qx), _ptr(qy), int(qx.shape[0]), _ptr(code), _stream(stream)))
+    return code
 
 
 def pip_set_rebuild(s: PolygonSet, opts=None, stream=None):

@@ -27,7 +27,8 @@ class PipError(RuntimeError):
 class BuildOpts(ctypes.Structure):
     _fields_ = [("cell_log2", I32), ("max_depth", I32), ("fanout_log2", I32), ("leaf_edges", I32),
                 ("size_ratio", I32), ("pts_per_cta", I32), ("stage_depth", I32), ("cand_mode", I32),
-                ("approx_units", I32)]
+                ("approx_units", I32), ("compact_edges", I32),
+                ("compact_early", I32)]
 
 
 class SetInfo(ctypes.Structure):
@@ -37,7 +38,8 @@ class SetInfo(ctypes.Structure):
                 ("leaf_cands", I64), ("leaf_edges", I64), ("index_bytes", I64),
                 ("max_blob_bytes", I64), ("cell_log2", I32), ("fanout_log2", I32), ("depth", I32),
                 ("cand_mode", I32), ("pts_per_cta", I32), ("stage_depth", I32), ("grid_x0", I32),
-                ("grid_y0", I32), ("grid_nx", I64), ("grid_ny", I64), ("build_ms", ctypes.c_double)]
+                ("grid_y0", I32), ("grid_nx", I64), ("grid_ny", I64), ("build_ms", ctypes.c_double),
+                ("compact_leaves", I64), ("compact_bytes", I64), ("compact_by_edges", I64 * 8)]
 
 
 class ProjectStats(ctypes.Structure):
@@ -96,6 +98,7 @@ SIGNATURES = {
     "pip_set_top_candidates": (I32, [P, I32, P, P, I64]),
     "pip_profile_enable": (I32, [P, I32]),
     "pip_profile_read": (I32, [P, P, P, P, P]),
+    "pip_locate": (I32, [P, P, P, I64, P, P]),
     "pip_kernel_launches": (I64, []),
     "pip_last_error": (ctypes.c_char_p, []),
     "pip_version": (I32, []),

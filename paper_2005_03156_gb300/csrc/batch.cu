@@ -152,7 +152,9 @@ __device__ __forceinline__ void batch_test_chunk(const DevSet* sets, uint32_t n_
   }
 }
 
-template <int STAGED>
+// COMPACT = false when no set of the run holds compact leaves (a leaner
+// trie step: the kernel is sensitive to its code size and registers).
+template <int STAGED, bool COMPACT>
 __global__ void __launch_bounds__(B_THREADS, 3) k_batch(PlanBufs B) {
   extern __shared__ __align__(128) uint4 stage_mem[];
   __shared__ __align__(8) uint64_t bar;
@@ -271,11 +273,13 @@ __global__ void __launch_bounds__(B_THREADS, 3) k_batch(PlanBufs B) {
           res.put(leaf, qx, qy, d, [&](int j) { return code0 + z[j]; }, B.queue, B.ctr + 0, B.hist, slot_add);
         if (__any_sync(full, split != 0u)) tr.push(split, qx, qy, z, d, sh);
 #pragma unroll 1
-        while (tr.count >= 128u) tr.step(128u, ix, pol, out, code0, res, B.queue, B.ctr + 0, B.hist, slot_add);
+        while (tr.count >= 128u)
+          tr.step<COMPACT>(128u, ix, pol, out, code0, res, B.queue, B.ctr + 0, B.hist, slot_add);
       }
 #pragma unroll 1
       while (tr.count > 0u)
-        tr.step(tr.count < 128u ? tr.count : 128u, ix, pol, out, code0, res, B.queue, B.ctr + 0, B.hist, slot_add);
+        tr.step<COMPACT>(tr.count < 128u ? tr.count : 128u, ix, pol, out, code0, res, B.queue, B.ctr + 0, B.hist,
+                         slot_add);
     }
     res.finish(B.queue, B.ctr + 5);
   }
@@ -396,6 +400,7 @@ struct pip_plan_s {
   int64_t sb_cap = 0;
   int grid = 0;
   int staged = 0;      // 0 unstaged, 1 staged
+  bool compact = false;  // the captured kernel handles compact leaves
   uint32_t ppc = 256;
   uint32_t stage_bytes = 16 * 1024;  // small: the one kernel's other phases want L1
   Alloc alloc;
@@ -446,15 +451,18 @@ static pip_status plan_alloc_sb(pip_plan_s* P, int64_t need, cudaStream_t s) {
 
 static int batch_smem(int staged, uint32_t stage_bytes) { return staged ? (int)stage_bytes : 0; }
 
+// The kernel instantiation for the plan's knobs.
+static void (*batch_kernel(int staged, bool compact))(PlanBufs) {
+  if (staged) return compact ? k_batch<1, true> : k_batch<1, false>;
+  return compact ? k_batch<0, true> : k_batch<0, false>;
+}
+
 static pip_status plan_grid(pip_plan_s* P) {
   int occ = 0;
   const int smem = batch_smem(P->staged, P->stage_bytes);
-  if (P->staged) {
-    PIP_CUDA(cudaFuncSetAttribute(k_batch<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    PIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<1>, B_THREADS, smem));
-  } else {
-    PIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_batch<0>, B_THREADS, 0));
-  }
+  auto k = batch_kernel(P->staged, P->compact);
+  if (P->staged) PIP_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  PIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, B_THREADS, smem));
   if (occ < 1) return fail(PIP_ECUDA, "pip_plan: batched kernel does not fit an SM");
   P->grid = num_sms() * occ;
   return PIP_OK;
@@ -481,10 +489,7 @@ static pip_status plan_capture(pip_plan_s* P, int t, cudaStream_t s) {
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (P->staged)
-      e = cudaLaunchKernelEx(&cfg, k_batch<1>, P->bufs);
-    else
-      e = cudaLaunchKernelEx(&cfg, k_batch<0>, P->bufs);
+    e = cudaLaunchKernelEx(&cfg, batch_kernel(P->staged, P->compact), P->bufs);
     cudaError_t e2 = cudaStreamEndCapture(cs, &P->graph[t]);
     if (e != cudaSuccess) res = cuda_fail(e, "pip_plan: cooperative launch capture");
     else if (e2 != cudaSuccess) res = cuda_fail(e2, "pip_plan: end capture");
@@ -521,14 +526,17 @@ extern "C" pip_status pip_plan_create(int64_t max_points, int32_t max_queries, v
   P->tables_bytes = align_up(P->off_tiles + sizeof(uint4) * (size_t)P->max_tiles, 256);
   Alloc* al = &P->alloc;
   // queue: max_points plus two reserved chunks per warp of the largest grid
-  int occ0 = 0, occ1 = 0;
-  PIP_CUDA(cudaFuncSetAttribute(k_batch<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                batch_smem(1, P->stage_bytes)));
-  PIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, k_batch<0>, B_THREADS, 0));
-  PIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_batch<1>, B_THREADS,
-                                                         batch_smem(1, P->stage_bytes)));
-  const int64_t queue_len =
-      max_points + 2 * (int64_t)QCHUNK * (B_THREADS / 32) * num_sms() * std::max(1, std::max(occ0, occ1));
+  int occ_max = 1;
+  for (int staged = 0; staged < 2; ++staged)
+    for (int compact = 0; compact < 2; ++compact) {
+      auto k = batch_kernel(staged, compact != 0);
+      int occ = 0;
+      if (staged)
+        PIP_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, batch_smem(1, P->stage_bytes)));
+      PIP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, B_THREADS, batch_smem(staged, P->stage_bytes)));
+      occ_max = std::max(occ_max, occ);
+    }
+  const int64_t queue_len = max_points + 2 * (int64_t)QCHUNK * (B_THREADS / 32) * num_sms() * occ_max;
   if (queue_len >= (1ll << 32)) return fail(PIP_EINVAL, "pip_plan_create: max_points too large");
   if (!P->tables.alloc(al, P->tables_bytes, s) || !P->queue.alloc(al, queue_len, s) ||
       !P->binned.alloc(al, max_points, s) || !P->ctr.alloc(al, 8, s) || !P->status.alloc(al, 2, s))
@@ -606,9 +614,20 @@ extern "C" pip_status pip_plan_run(pip_plan plan, const pip_query* q, int32_t n_
   RunHeader H{};
   uint8_t* h = plan->host_tables[t];
   DevSet* hs = (DevSet*)(h + plan->off_sets);
+  bool any_compact = false;
   for (size_t i = 0; i < sets.size(); ++i) {
     hs[i].view = sets[i]->view;
     hs[i].sb_base = sb_base[i];
+    any_compact |= sets[i]->view.compact != 0;
+  }
+  if (any_compact != plan->compact) {  // the other kernel instantiation: capture again
+    PIP_CUDA(cudaDeviceSynchronize());
+    plan->drop_graphs();
+    plan->compact = any_compact;
+    st = plan_grid(plan);
+    if (st != PIP_OK) return st;
+    if (!plan->partial.alloc(&plan->alloc, (size_t)plan->grid + 1, s))
+      return fail(PIP_ENOMEM, "pip_plan: partials");
   }
   DevQuery* hq = (DevQuery*)(h + plan->off_q);
   uint32_t* hqoff = (uint32_t*)(h + plan->off_qoff);

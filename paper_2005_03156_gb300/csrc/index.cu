@@ -409,7 +409,7 @@ __global__ void k_classify(int64_t n_cell, const uint64_t* __restrict__ fc_coff,
                            uint32_t* __restrict__ fc_ne, uint32_t* __restrict__ fc_leaf,
                            uint32_t* __restrict__ fc_split, int32_t* __restrict__ fc_val, int shift,
                            int can_split, uint32_t leaf_edges, int size_ratio, long long approx,
-                           unsigned long long* counters) {
+                           int compact_early, unsigned long long* counters) {
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cell;
        c += (int64_t)gridDim.x * blockDim.x) {
     uint32_t nk = 0, ne = 0, first = 0xFFFFFFFFu;
@@ -451,7 +451,9 @@ __global__ void k_classify(int64_t n_cell, const uint64_t* __restrict__ fc_coff,
       ne = 0;
     } else {
       const long long side = 1ll << shift;
-      const bool want = ne > leaf_edges || (size_ratio > 0 && side * size_ratio > min_ext) ||
+      // compact_early: every boundary cell splits until it is compact
+      // (decided once its edges are known) or the deepest level is reached
+      const bool want = compact_early || ne > leaf_edges || (size_ratio > 0 && side * size_ratio > min_ext) ||
                         (approx > 0 && side > approx);
       if (can_split && want) {
         split = 1;
@@ -470,9 +472,14 @@ __global__ void k_classify(int64_t n_cell, const uint64_t* __restrict__ fc_coff,
 // Children of one split cell (frontier cells p*16 .. p*16+15): give each
 // EMPTY / INTERIOR child a 2-bit code into the node's 4-entry palette. A
 // child whose value does not fit the palette becomes a leaf instead (its
-// one full candidate, or none, then answers through the crossing test).
+// one full candidate, or none, then answers through the crossing test), or,
+// with compact leaves, a one-slot compact record holding that value
+// (fcomp = 1 | COMP_CONST). Parent p's node is nodes[node_slot[p]].
+constexpr uint32_t COMP_CONST = 0x100u;
+
 __global__ void k_palette(int64_t n_parent, uint32_t* __restrict__ fc_leaf,
-                          const uint32_t* __restrict__ fc_split, const int32_t* __restrict__ fc_val,
+                          const uint32_t* __restrict__ fc_split, uint32_t* __restrict__ fc_comp,
+                          const int32_t* __restrict__ fc_val, const uint32_t* __restrict__ node_slot,
                           TrieNode* __restrict__ nodes, unsigned long long* counters) {
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_parent;
        p += (int64_t)gridDim.x * blockDim.x) {
@@ -481,13 +488,14 @@ __global__ void k_palette(int64_t n_parent, uint32_t* __restrict__ fc_leaf,
     int np = 0;
     for (int sub = 0; sub < NODE_FAN; ++sub) {
       const int64_t c = p * NODE_FAN + sub;
-      if (fc_leaf[c] || fc_split[c]) continue;
+      if (fc_leaf[c] || fc_split[c] || (fc_comp && fc_comp[c])) continue;
       const int32_t v = fc_val[c];
       int j = 0;
       while (j < np && pal[j] != v) ++j;
       if (j == np) {
         if (np == 4) {
-          fc_leaf[c] = 1;
+          if (fc_comp) fc_comp[c] = 1u | COMP_CONST;
+          else fc_leaf[c] = 1;
           atomicAdd(counters + 2, 1ull);
           continue;
         }
@@ -495,36 +503,46 @@ __global__ void k_palette(int64_t n_parent, uint32_t* __restrict__ fc_leaf,
       }
       codes |= (uint32_t)j << (2 * sub);
     }
-    TrieNode& nd = nodes[p];
+    TrieNode& nd = nodes[node_slot[p]];
     nd.codes = codes;
     for (int j = 0; j < 4; ++j) nd.pal[j] = pal[j];
   }
 }
 
 // Leaf / split masks and rank bases of each node (after the ranks exist).
+// Compact children set both bits and add (slots - 1) as their code; split
+// and compact children are numbered together from child_base (the first
+// one's global slot), compact ones taking their record's slots.
 __global__ void k_node_finish(int64_t n_parent, const uint32_t* __restrict__ fc_leaf,
-                              const uint32_t* __restrict__ fc_split,
+                              const uint32_t* __restrict__ fc_split, const uint32_t* __restrict__ fc_comp,
                               const uint64_t* __restrict__ leaf_rank,
-                              const uint64_t* __restrict__ split_rank, uint32_t slot_base,
-                              uint64_t node_base, TrieNode* __restrict__ nodes) {
+                              const uint64_t* __restrict__ slot_rank, uint32_t slot_base,
+                              uint64_t level_base, const uint32_t* __restrict__ node_slot,
+                              TrieNode* __restrict__ nodes) {
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n_parent;
        p += (int64_t)gridDim.x * blockDim.x) {
-    uint32_t lm = 0, cm = 0;
-    int64_t first_leaf = -1, first_split = -1;
+    uint32_t lm = 0, cm = 0, ccodes = 0;
+    int64_t first_leaf = -1, first_child = -1;
     for (int sub = 0; sub < NODE_FAN; ++sub) {
       const int64_t c = p * NODE_FAN + sub;
+      const uint32_t comp = fc_comp ? (fc_comp[c] & 0xFFu) : 0u;
       if (fc_leaf[c]) {
         lm |= 1u << sub;
         if (first_leaf < 0) first_leaf = c;
-      } else if (fc_split[c]) {
+      } else if (fc_split[c] || comp) {
         cm |= 1u << sub;
-        if (first_split < 0) first_split = c;
+        if (comp) {
+          lm |= 1u << sub;
+          ccodes |= (comp - 1u) << (2 * sub);
+        }
+        if (first_child < 0) first_child = c;
       }
     }
-    TrieNode& nd = nodes[p];
+    TrieNode& nd = nodes[node_slot[p]];
     nd.masks = lm | (cm << 16);
+    nd.codes |= ccodes;
     nd.leaf_base = first_leaf >= 0 ? slot_base + (uint32_t)leaf_rank[first_leaf] : 0u;
-    nd.child_base = first_split >= 0 ? (uint32_t)(node_base + split_rank[first_split]) : 0u;
+    nd.child_base = first_child >= 0 ? (uint32_t)(level_base + slot_rank[first_child]) : 0u;
   }
 }
 
@@ -535,31 +553,20 @@ __global__ void k_eff_nk(int64_t n, const uint32_t* __restrict__ fc_nk, const ui
     out[c] = (fc_leaf[c] | fc_split[c]) ? fc_nk[c] : 0u;
 }
 
-// Boundary cells: write LEAF / CHILD descriptors, record leaf -> cell, and
-// compact kept candidates (poly, base, kept count, source) in cell order.
-__global__ void k_boundary(int64_t n_cell, const uint64_t* __restrict__ fc_coff,
-                           const uint8_t* __restrict__ cd_keep, const int32_t* __restrict__ cd_poly,
-                           const uint8_t* __restrict__ cd_base, const uint32_t* __restrict__ cd_kept,
-                           const uint64_t* __restrict__ cd_src, const uint32_t* __restrict__ cd_srcn,
-                           const uint32_t* __restrict__ fc_slot, const uint32_t* __restrict__ fc_leaf,
-                           const uint32_t* __restrict__ fc_split, const uint64_t* __restrict__ leaf_rank,
-                           const uint64_t* __restrict__ split_rank, const uint64_t* __restrict__ kc_off,
-                           uint32_t* __restrict__ desc, uint32_t slot_base, uint64_t child_base,
-                           int fan, uint32_t* __restrict__ leaf_cell, int32_t* __restrict__ kc_poly,
-                           uint8_t* __restrict__ kc_base, uint32_t* __restrict__ kc_cnt,
-                           uint64_t* __restrict__ kc_src, uint32_t* __restrict__ kc_srcn,
-                           uint32_t* __restrict__ kc_cell) {
+// Boundary cells (leaf or split so far): compact their kept candidates
+// (poly, base, kept count, source) in cell order.
+__global__ void k_boundary_kc(int64_t n_cell, const uint64_t* __restrict__ fc_coff,
+                              const uint8_t* __restrict__ cd_keep, const int32_t* __restrict__ cd_poly,
+                              const uint8_t* __restrict__ cd_base, const uint32_t* __restrict__ cd_kept,
+                              const uint64_t* __restrict__ cd_src, const uint32_t* __restrict__ cd_srcn,
+                              const uint32_t* __restrict__ fc_leaf, const uint32_t* __restrict__ fc_split,
+                              const uint64_t* __restrict__ kc_off, int32_t* __restrict__ kc_poly,
+                              uint8_t* __restrict__ kc_base, uint32_t* __restrict__ kc_cnt,
+                              uint64_t* __restrict__ kc_src, uint32_t* __restrict__ kc_srcn,
+                              uint32_t* __restrict__ kc_cell) {
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cell;
        c += (int64_t)gridDim.x * blockDim.x) {
-    const bool leaf = fc_leaf[c], split = fc_split[c];
-    if (!leaf && !split) continue;
-    if (leaf) {
-      const uint64_t r = leaf_rank[c];
-      if (desc) desc[fc_slot[c]] = make_desc(TAG_LEAF, slot_base + (uint32_t)r);
-      leaf_cell[r] = (uint32_t)c;
-    } else if (desc) {
-      desc[fc_slot[c]] = make_desc(TAG_CHILD, (uint32_t)(child_base + split_rank[c]));
-    }
+    if (!fc_leaf[c] && !fc_split[c]) continue;
     uint64_t w = kc_off[c];
     for (uint64_t i = fc_coff[c]; i < fc_coff[c + 1]; ++i) {
       if (!cd_keep[i]) continue;
@@ -570,6 +577,141 @@ __global__ void k_boundary(int64_t n_cell, const uint64_t* __restrict__ fc_coff,
       kc_srcn[w] = cd_srcn ? cd_srcn[i] : 0;
       kc_cell[w] = (uint32_t)c;
       ++w;
+    }
+  }
+}
+
+// Descriptors of this level's boundary cells (top level only: deeper levels
+// are described by their parents' nodes) and leaf -> cell for the blobs.
+__global__ void k_boundary_desc(int64_t n_cell, const uint32_t* __restrict__ fc_slot,
+                                const uint32_t* __restrict__ fc_leaf, const uint32_t* __restrict__ fc_split,
+                                const uint32_t* __restrict__ fc_comp, const uint64_t* __restrict__ leaf_rank,
+                                const uint64_t* __restrict__ slot_rank, uint32_t* __restrict__ desc,
+                                uint32_t slot_base, uint64_t level_base, uint32_t* __restrict__ leaf_cell) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cell;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t comp = fc_comp ? (fc_comp[c] & 0xFFu) : 0u;
+    if (fc_leaf[c]) {
+      const uint64_t r = leaf_rank[c];
+      if (desc) desc[fc_slot[c]] = make_desc(TAG_LEAF, slot_base + (uint32_t)r);
+      leaf_cell[r] = (uint32_t)c;
+    } else if (desc && fc_split[c]) {
+      desc[fc_slot[c]] = make_desc(TAG_CHILD, (uint32_t)(level_base + slot_rank[c]));
+    } else if (desc && comp) {
+      desc[fc_slot[c]] = make_desc(TAG_CHILD, DESC_COMPACT | ((comp - 1u) << DESC_SLOTS_SHIFT) |
+                                                  (uint32_t)(level_base + slot_rank[c]));
+    }
+  }
+}
+
+// Distinct non-horizontal kept edges of a boundary cell and each kept
+// candidate's mask over them (horizontal edges never count, so they drop
+// out). Candidates that are never inside (mask 0, base 0) are skipped, and
+// one that is inside everywhere (mask 0, base 1) ends the list. Returns
+// false when the cell does not fit a compact record (more than max_edges
+// edges, more than COMPACT_MAX_CANDS candidates, or an id above 24 bits).
+__device__ bool compact_gather(uint64_t k0, uint64_t k1, const int32_t* __restrict__ kc_poly,
+                               const uint8_t* __restrict__ kc_base, const uint32_t* __restrict__ kc_cnt,
+                               const uint64_t* __restrict__ kc_eoff, const int4* __restrict__ kedges,
+                               int max_edges, int4 (&edge)[COMPACT_MAX_EDGES], uint32_t& ne,
+                               uint32_t (&cand)[COMPACT_MAX_CANDS], uint32_t& nc) {
+  ne = 0;
+  nc = 0;
+  for (uint64_t i = k0; i < k1; ++i) {
+    uint32_t mask = 0;
+    for (uint64_t e = kc_eoff[i]; e < kc_eoff[i] + kc_cnt[i]; ++e) {
+      const int4 v = kedges[e];
+      if (v.y == v.w) continue;
+      uint32_t k = 0;
+      while (k < ne && !(edge[k].x == v.x && edge[k].y == v.y && edge[k].z == v.z && edge[k].w == v.w)) ++k;
+      if (k == ne) {
+        if ((int)ne >= max_edges) return false;
+        edge[ne++] = v;
+      }
+      mask ^= 1u << k;
+    }
+    const uint32_t base = kc_base[i] & 1u;
+    if (mask == 0u && !base) continue;
+    if (nc >= (uint32_t)COMPACT_MAX_CANDS || (uint32_t)kc_poly[i] > CAND_ID_MASK) return false;
+    cand[nc++] = (uint32_t)kc_poly[i] | (mask << 24) | (base << 31);
+    if (mask == 0u) break;
+  }
+  return true;
+}
+
+// Which boundary cells become compact leaves: fc_comp = record slots (0 =
+// not compact); a compact cell is no longer a leaf or split. Without
+// `early` only leaves are considered (the trie keeps its shape and compact
+// records replace residual leaves); with it, a cell that would split stops
+// as soon as it fits a record.
+__global__ void k_compact_check(int64_t n_cell, int early, uint32_t* __restrict__ fc_leaf,
+                                uint32_t* __restrict__ fc_split,
+                                const uint64_t* __restrict__ kc_off, const int32_t* __restrict__ kc_poly,
+                                const uint8_t* __restrict__ kc_base, const uint32_t* __restrict__ kc_cnt,
+                                const uint64_t* __restrict__ kc_eoff, const int4* __restrict__ kedges,
+                                int max_edges, uint32_t* __restrict__ fc_comp,
+                                unsigned long long* counters) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cell;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    fc_comp[c] = 0;
+    if (!fc_leaf[c] && !(early && fc_split[c])) continue;
+    int4 edge[COMPACT_MAX_EDGES];
+    uint32_t cand[COMPACT_MAX_CANDS];
+    uint32_t ne = 0, nc = 0;
+    if (!compact_gather(kc_off[c], kc_off[c + 1], kc_poly, kc_base, kc_cnt, kc_eoff, kedges, max_edges,
+                        edge, ne, cand, nc))
+      continue;
+    const uint32_t slots = compact_slots_for(ne);
+    fc_comp[c] = slots;
+    fc_leaf[c] = 0;
+    fc_split[c] = 0;
+    atomicAdd(counters + 3, 1ull);
+    atomicAdd(counters + 4, (unsigned long long)slots);
+    atomicAdd(counters + 5 + ne, 1ull);
+  }
+}
+
+// Slots a frontier cell takes in its level's node array: a split cell one
+// (its trie node), a compact cell its record's slots.
+__global__ void k_slot_size(int64_t n_cell, const uint32_t* __restrict__ fc_split,
+                            const uint32_t* __restrict__ fc_comp, uint32_t* __restrict__ out) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cell;
+       c += (int64_t)gridDim.x * blockDim.x)
+    out[c] = fc_split[c] ? 1u : (fc_comp ? (fc_comp[c] & 0xFFu) : 0u);
+}
+
+// Write the compact records of this level (level array `rec`, local slots).
+__global__ void k_compact_fill(int64_t n_cell, const uint32_t* __restrict__ fc_comp,
+                               const int32_t* __restrict__ fc_val, const uint64_t* __restrict__ slot_rank,
+                               const uint64_t* __restrict__ kc_off, const int32_t* __restrict__ kc_poly,
+                               const uint8_t* __restrict__ kc_base, const uint32_t* __restrict__ kc_cnt,
+                               const uint64_t* __restrict__ kc_eoff, const int4* __restrict__ kedges,
+                               int max_edges, uint32_t* __restrict__ rec) {
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cell;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t comp = fc_comp[c];
+    if (!comp) continue;
+    int4 edge[COMPACT_MAX_EDGES];
+    uint32_t cand[COMPACT_MAX_CANDS];
+    uint32_t ne = 0, nc = 0;
+    if (comp & COMP_CONST) {  // a constant child that did not fit its parent's palette
+      const int32_t v = fc_val[c];
+      if (v >= 0) cand[nc++] = (uint32_t)v | (1u << 31);
+    } else {
+      compact_gather(kc_off[c], kc_off[c + 1], kc_poly, kc_base, kc_cnt, kc_eoff, kedges, max_edges, edge,
+                     ne, cand, nc);
+    }
+    uint32_t* w = rec + 8 * slot_rank[c];
+    const uint32_t nw = 8u * (comp & 0xFFu);
+    for (uint32_t k = 0; k < nw; ++k) w[k] = 0u;
+    w[0] = ne | (nc << 3);
+    for (uint32_t i = 0; i < nc; ++i) w[1 + i] = cand[i];
+    for (uint32_t k = 0; k < ne; ++k) {
+      uint32_t* e = w + 4 + 4 * k;
+      e[0] = (uint32_t)edge[k].x;
+      e[1] = (uint32_t)edge[k].y;
+      e[2] = (uint32_t)edge[k].z;
+      e[3] = (uint32_t)edge[k].w;
     }
   }
 }
@@ -731,6 +873,14 @@ __global__ void k_gather_u32(const uint32_t* __restrict__ flags, const uint64_t*
     if (flags[i]) out[rank[i]] = (uint32_t)i;
 }
 
+// Local node slot of each split cell (split cells in rank order).
+__global__ void k_split_slot(int64_t n_split, const uint32_t* __restrict__ split_cells,
+                             const uint64_t* __restrict__ slot_rank, uint32_t* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_split;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (uint32_t)slot_rank[split_cells[i]];
+}
+
 __global__ void k_add_u32(uint2* p, int64_t n, uint32_t add) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
@@ -816,6 +966,13 @@ static void resolve_opts(const pip_build_opts& in, int64_t n_poly, long long w, 
   if (o.stage_depth < 0) o.stage_depth = -1;  // no shared-memory staging
   if (o.stage_depth > 2) o.stage_depth = 2;
   if (o.cand_mode <= 0) o.cand_mode = n_levels > 0 ? 1 : 2;
+  // compact leaves: off unless asked for (compact_edges 1..7); also off in
+  // approximate mode (whose leaves answer without a test) and when ids do
+  // not fit a compact candidate word
+  if (o.compact_edges == 0) o.compact_edges = -1;  // measured slower on the state workload: off
+  if (o.compact_edges > COMPACT_MAX_EDGES) o.compact_edges = COMPACT_MAX_EDGES;
+  if (o.approx_units > 0 || n_poly > (int64_t)CAND_ID_MASK + 1) o.compact_edges = -1;
+  o.compact_early = (o.compact_edges > 0 && o.compact_early > 0) ? 1 : 0;
 }
 
 // Build the hierarchy arrays on the device.
@@ -958,8 +1115,8 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
 
   unsigned long long* counters = nullptr;  // [0] empty, [1] interior, [2] palette overflows
   DBuf<unsigned long long> cnt_buf;
-  ALLOC(cnt_buf, 3);
-  PIP_CUDA(cudaMemsetAsync(cnt_buf.p, 0, 4 * sizeof(unsigned long long), s));
+  ALLOC(cnt_buf, 13);  // [3] compact cells [4] compact slots [5 + E] compact cells by edge count
+  PIP_CUDA(cudaMemsetAsync(cnt_buf.p, 0, 14 * sizeof(unsigned long long), s));
   counters = cnt_buf.p;
 
   // per-level outputs
@@ -972,7 +1129,6 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
   std::vector<DBuf<TrieNode>> node_lv;  // nodes of each level's split cells
   std::vector<int64_t> node_len;
   int64_t table_total = top_cells;
-  int64_t node_total = 0;
   desc_lv.emplace_back();
   ALLOC(desc_lv[0], top_cells);
   PIP_CUDA(cudaMemsetAsync(desc_lv[0].p, 0, (top_cells + 1) * sizeof(uint32_t), s));
@@ -1013,10 +1169,13 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
   top_cnt.release();
   top_coff.release();
 
-  DBuf<int4> src_edges;  // parent's kept edges (level > 0)
+  DBuf<int4> src_edges;         // parent's kept edges (level > 0)
+  DBuf<uint32_t> split_slot_prev;  // node slot of each split cell of the previous level
   uint32_t slot_base = 0;
   int64_t sb_total = 0, blob_total16 = 0, max_blob16 = 0, leaf_cands = 0, leaf_edges = 0;
+  int64_t level_base = 0;  // global node-array slot of this level's first entry
   int depth_used = 0;
+  const bool compact = o.compact_edges > 0;
   for (int lv = 0; n_cell > 0; ++lv) {
     depth_used = lv;
     const int shift = g.s0 - lv * k;
@@ -1037,7 +1196,7 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
     }
     PIP_CUDA(cudaGetLastError());
     // classify
-    DBuf<uint32_t> fnk, fne, fleaf, fsplit, fnk_eff;
+    DBuf<uint32_t> fnk, fne, fleaf, fsplit, fnk_eff, fcomp, fsize;
     DBuf<int32_t> fval;
     ALLOC(fnk, n_cell);
     ALLOC(fne, n_cell);
@@ -1045,50 +1204,42 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
     ALLOC(fsplit, n_cell);
     ALLOC(fval, n_cell);
     ALLOC(fnk_eff, n_cell);
+    ALLOC(fcomp, n_cell);
+    ALLOC(fsize, n_cell);
+    PIP_CUDA(cudaMemsetAsync(fcomp.p, 0, (n_cell + 1) * sizeof(uint32_t), s));
     k_classify<<<blocks_for(n_cell), TB, 0, s>>>(n_cell, fcoff.p, cd_poly.p, cd_kept.p, cd_base.p,
                                                  cd_keep.p, S->poly_box.p, fslot.p,
                                                  lv == 0 ? desc_lv[0].p : nullptr, fnk.p, fne.p, fleaf.p,
                                                  fsplit.p, fval.p, shift, can_split ? 1 : 0,
                                                  (uint32_t)o.leaf_edges, o.size_ratio,
-                                                 (long long)o.approx_units, counters);
+                                                 (long long)o.approx_units, compact ? o.compact_early : 0,
+                                                 counters);
     PIP_CUDA(cudaGetLastError());
     const int64_t n_parent = lv == 0 ? 0 : n_cell / fan;
-    if (lv > 0) {  // palettes of the parents' nodes (may turn children into leaves)
-      k_palette<<<blocks_for(n_parent), TB, 0, s>>>(n_parent, fleaf.p, fsplit.p, fval.p,
-                                                    node_lv.back().p, counters);
+    if (lv > 0 && !compact) {  // palettes of the parents' nodes (may turn children into leaves)
+      k_palette<<<blocks_for(n_parent), TB, 0, s>>>(n_parent, fleaf.p, fsplit.p, nullptr, fval.p,
+                                                    split_slot_prev.p, node_lv.back().p, counters);
       PIP_CUDA(cudaGetLastError());
     }
     k_eff_nk<<<blocks_for(n_cell), TB, 0, s>>>(n_cell, fnk.p, fleaf.p, fsplit.p, fnk_eff.p);
     PIP_CUDA(cudaGetLastError());
-    // ranks
-    DBuf<uint64_t> leaf_rank, split_rank, kc_off, tots;
-    ALLOC(leaf_rank, n_cell + 1);
-    ALLOC(split_rank, n_cell + 1);
+    // kept candidates of the boundary cells, in cell order
+    DBuf<uint64_t> kc_off;
+    int64_t n_kc = 0;
     ALLOC(kc_off, n_cell + 1);
-    ALLOC(tots, 3);
-    PIP_CUDA(cudaMemsetAsync(fnk_eff.p + n_cell, 0, sizeof(uint32_t), s));
-    CHECK(scan_u32_to_u64(*al, fleaf.p, leaf_rank.p, n_cell, tots.p + 0, s));
-    CHECK(scan_u32_to_u64(*al, fsplit.p, split_rank.p, n_cell, tots.p + 1, s));
-    CHECK(scan_u32_to_u64(*al, fnk_eff.p, kc_off.p, n_cell + 1, tots.p + 2, s));
-    uint64_t t3[3];
-    CHECK(d2h(t3, tots.p, 3, s));
-    const int64_t n_leaf = (int64_t)t3[0], n_split = (int64_t)t3[1], n_kc = (int64_t)t3[2];
-    const uint64_t child_base = (uint64_t)(node_total + (lv > 0 ? node_len.back() : 0));
-    if (child_base + (uint64_t)n_split >= (1ull << 30) ||
-        (uint64_t)slot_base + (uint64_t)n_leaf + SB_SLOTS >= (1ull << 30))
-      return fail(PIP_ERANGE, "index build: index exceeds 2^30 entries; raise cell_log2");
-    if (lv > 0) {  // masks and bases of the parents' nodes
-      k_node_finish<<<blocks_for(n_parent), TB, 0, s>>>(n_parent, fleaf.p, fsplit.p, leaf_rank.p,
-                                                        split_rank.p, slot_base, child_base,
-                                                        node_lv.back().p);
-      PIP_CUDA(cudaGetLastError());
+    {
+      DBuf<uint64_t> tot;
+      ALLOC(tot, 1);
+      PIP_CUDA(cudaMemsetAsync(fnk_eff.p + n_cell, 0, sizeof(uint32_t), s));
+      CHECK(scan_u32_to_u64(*al, fnk_eff.p, kc_off.p, n_cell + 1, tot.p, s));
+      uint64_t t = 0;
+      CHECK(d2h(&t, tot.p, 1, s));
+      n_kc = (int64_t)t;
     }
-    // boundary cells: descriptors + kept candidate compaction
-    DBuf<uint32_t> leaf_cell, kc_cnt, kc_srcn, kc_cell;
+    DBuf<uint32_t> kc_cnt, kc_srcn, kc_cell;
     DBuf<int32_t> kc_poly;
     DBuf<uint8_t> kc_base;
     DBuf<uint64_t> kc_src, kc_eoff;
-    ALLOC(leaf_cell, n_leaf);
     ALLOC(kc_cnt, n_kc);
     ALLOC(kc_srcn, n_kc);
     ALLOC(kc_cell, n_kc);
@@ -1096,11 +1247,10 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
     ALLOC(kc_base, n_kc);
     ALLOC(kc_src, n_kc);
     ALLOC(kc_eoff, n_kc + 1);
-    k_boundary<<<blocks_for(n_cell), TB, 0, s>>>(
+    k_boundary_kc<<<blocks_for(n_cell), TB, 0, s>>>(
         n_cell, fcoff.p, cd_keep.p, cd_poly.p, cd_base.p, cd_kept.p, lv ? cd_src.p : nullptr,
-        lv ? cd_srcn.p : nullptr, fslot.p, fleaf.p, fsplit.p, leaf_rank.p, split_rank.p, kc_off.p,
-        lv == 0 ? desc_lv[0].p : nullptr, slot_base, child_base, fan, leaf_cell.p, kc_poly.p,
-        kc_base.p, kc_cnt.p, kc_src.p, kc_srcn.p, kc_cell.p);
+        lv ? cd_srcn.p : nullptr, fleaf.p, fsplit.p, kc_off.p, kc_poly.p, kc_base.p, kc_cnt.p, kc_src.p,
+        kc_srcn.p, kc_cell.p);
     PIP_CUDA(cudaGetLastError());
     // kept edges of every kept candidate
     uint64_t n_ke = 0;
@@ -1127,6 +1277,61 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
             g, shift, n_kc, kc_cell.p, fx.p, fy.p, kc_poly.p, kc_src.p, kc_srcn.p, src_edges.p,
             nullptr, nullptr, nullptr, nullptr, nullptr, dummy_base.p, kc_eoff.p, kedges.p);
       }
+      PIP_CUDA(cudaGetLastError());
+    }
+    if (compact) {  // compact leaves, then the parents' palettes (overflows become compact too)
+      k_compact_check<<<blocks_for(n_cell), TB, 0, s>>>(n_cell, o.compact_early, fleaf.p, fsplit.p, kc_off.p, kc_poly.p,
+                                                        kc_base.p, kc_cnt.p, kc_eoff.p, kedges.p,
+                                                        o.compact_edges, fcomp.p, counters);
+      PIP_CUDA(cudaGetLastError());
+      if (lv > 0) {
+        k_palette<<<blocks_for(n_parent), TB, 0, s>>>(n_parent, fleaf.p, fsplit.p, fcomp.p, fval.p,
+                                                      split_slot_prev.p, node_lv.back().p, counters);
+        PIP_CUDA(cudaGetLastError());
+      }
+    }
+    // ranks: leaf slots, split cells, node-array slots (split nodes + compact records)
+    k_slot_size<<<blocks_for(n_cell), TB, 0, s>>>(n_cell, fsplit.p, compact ? fcomp.p : nullptr, fsize.p);
+    PIP_CUDA(cudaGetLastError());
+    DBuf<uint64_t> leaf_rank, split_rank, slot_rank, tots;
+    ALLOC(leaf_rank, n_cell + 1);
+    ALLOC(split_rank, n_cell + 1);
+    ALLOC(slot_rank, n_cell + 1);
+    ALLOC(tots, 3);
+    CHECK(scan_u32_to_u64(*al, fleaf.p, leaf_rank.p, n_cell, tots.p + 0, s));
+    CHECK(scan_u32_to_u64(*al, fsplit.p, split_rank.p, n_cell, tots.p + 1, s));
+    CHECK(scan_u32_to_u64(*al, fsize.p, slot_rank.p, n_cell, tots.p + 2, s));
+    uint64_t t3[3];
+    CHECK(d2h(t3, tots.p, 3, s));
+    const int64_t n_leaf = (int64_t)t3[0], n_split = (int64_t)t3[1], n_slots_lv = (int64_t)t3[2];
+    if ((uint64_t)level_base + (uint64_t)n_slots_lv >= (uint64_t)SLOT_MASK ||
+        (uint64_t)slot_base + (uint64_t)n_leaf + SB_SLOTS >= (1ull << 30))
+      return fail(PIP_ERANGE, "index build: trie or leaves exceed their 27 / 30-bit indices; raise cell_log2");
+    if (lv > 0) {  // masks and bases of the parents' nodes
+      k_node_finish<<<blocks_for(n_parent), TB, 0, s>>>(n_parent, fleaf.p, fsplit.p,
+                                                        compact ? fcomp.p : nullptr, leaf_rank.p,
+                                                        slot_rank.p, slot_base, (uint64_t)level_base,
+                                                        split_slot_prev.p, node_lv.back().p);
+      PIP_CUDA(cudaGetLastError());
+    }
+    // top-level descriptors of boundary cells, leaf -> cell
+    DBuf<uint32_t> leaf_cell;
+    ALLOC(leaf_cell, n_leaf);
+    k_boundary_desc<<<blocks_for(n_cell), TB, 0, s>>>(n_cell, fslot.p, fleaf.p, fsplit.p,
+                                                      compact ? fcomp.p : nullptr, leaf_rank.p, slot_rank.p,
+                                                      lv == 0 ? desc_lv[0].p : nullptr, slot_base,
+                                                      (uint64_t)level_base, leaf_cell.p);
+    PIP_CUDA(cudaGetLastError());
+    // this level's node array: the split cells' nodes (filled while their
+    // children are classified at the next level) and the compact records
+    node_lv.emplace_back();
+    ALLOC(node_lv.back(), n_slots_lv);
+    PIP_CUDA(cudaMemsetAsync(node_lv.back().p, 0, (n_slots_lv + 1) * sizeof(TrieNode), s));
+    node_len.push_back(n_slots_lv);
+    if (compact && n_slots_lv > 0) {
+      k_compact_fill<<<blocks_for(n_cell), TB, 0, s>>>(n_cell, fcomp.p, fval.p, slot_rank.p, kc_off.p,
+                                                       kc_poly.p, kc_base.p, kc_cnt.p, kc_eoff.p, kedges.p,
+                                                       o.compact_edges, (uint32_t*)node_lv.back().p);
       PIP_CUDA(cudaGetLastError());
     }
     // leaves of this level -> superbin blobs
@@ -1168,19 +1373,19 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
       blob_total16 += (int64_t)total16;
       sb_total += n_sb;
     }
-    // leaf candidates / edges totals (stats)
-    {
-      DBuf<uint32_t> leafnk;
-      (void)leafnk;
-    }
     slot_base += (uint32_t)(n_sb * SB_SLOTS);
-    leaf_cands += 0;
     // next frontier from split cells
-    if (n_split == 0) break;
+    if (n_split == 0) {
+      level_base += n_slots_lv;
+      break;
+    }
     const int64_t n_child = n_split * fan;
-    DBuf<uint32_t> split_cells;
+    DBuf<uint32_t> split_cells, split_slot;
     ALLOC(split_cells, n_split);
+    ALLOC(split_slot, n_split);
     k_gather_u32<<<blocks_for(n_cell), TB, 0, s>>>(fsplit.p, split_rank.p, n_cell, split_cells.p);
+    k_split_slot<<<blocks_for(n_split), TB, 0, s>>>(n_split, split_cells.p, slot_rank.p, split_slot.p);
+    PIP_CUDA(cudaGetLastError());
     DBuf<uint32_t> ccount;
     DBuf<uint64_t> coff, tot;
     ALLOC(ccount, n_child);
@@ -1214,12 +1419,6 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
         kc_eoff.p, S->poly_box.p, nullptr, coff.p, nfx.p, nfy.p, nslot.p, ncell.p, npoly.p, nbase.p,
         nsrc.p, nsrcn.p);
     PIP_CUDA(cudaGetLastError());
-    // the nodes of this level's split cells (filled while their children are classified)
-    node_total = (int64_t)child_base;
-    node_lv.emplace_back();
-    ALLOC(node_lv.back(), n_split);
-    PIP_CUDA(cudaMemsetAsync(node_lv.back().p, 0, (n_split + 1) * sizeof(TrieNode), s));
-    node_len.push_back(n_split);
     // advance
     fx = std::move(nfx);
     fy = std::move(nfy);
@@ -1231,8 +1430,10 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
     cd_src = std::move(nsrc);
     cd_srcn = std::move(nsrcn);
     src_edges = std::move(kedges);
+    split_slot_prev = std::move(split_slot);
     n_cell = n_child;
     n_cand = (int64_t)n_cc;
+    level_base += n_slots_lv;
     PIP_CUDA(cudaStreamSynchronize(s));
   }
 
@@ -1285,8 +1486,8 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
   }
   uint32_t e2 = 0;
   CHECK(d2h(&e2, err.p, 1, s));
-  unsigned long long hc[3];
-  CHECK(d2h(hc, counters, 3, s));
+  unsigned long long hc[13];
+  CHECK(d2h(hc, counters, 13, s));
   PIP_CUDA(cudaEventRecord(ev1, s));
   PIP_CUDA(cudaEventSynchronize(ev1));
   float ms = 0;
@@ -1307,6 +1508,7 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
   v.blobs = S->blobs.p;
   v.sbdesc = S->sbdesc.p;
   v.approx_id = S->approx.p;  // nullptr unless approximate
+  v.compact = hc[3] > 0 ? 1u : 0u;
   {  // L2-resident part of the trie: the top grid plus the first nodes (the
      // shallow levels come first) up to three quarters of the L2
     int dev = 0, l2 = 0;
@@ -1334,6 +1536,9 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
   I.leaf_edges = leaf_edges;
   I.index_bytes = top_cells * 4 + n_nodes * 32 + blob_total16 * 16 + sb_total * 8;
   I.max_blob_bytes = max_blob16 * 16;
+  I.compact_leaves = (int64_t)hc[3];
+  I.compact_bytes = (int64_t)hc[4] * 32;
+  for (int e = 0; e < 8; ++e) I.compact_by_edges[e] = (int64_t)hc[5 + e];
   I.cell_log2 = g.s0;
   I.fanout_log2 = k;
   I.depth = depth_used;

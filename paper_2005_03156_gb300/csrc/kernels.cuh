@@ -64,12 +64,18 @@ __device__ __forceinline__ void lookup4(const IndexView& ix, const int32_t (&qx)
     NodeWords nw[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j)  // issue the node loads of all four points first
-      if ((d[j] >> 30) == TAG_CHILD) nw[j] = ld_node(ix.nodes, d[j] & PAYLOAD_MASK, pol);
+      if ((d[j] >> 30) == TAG_CHILD) nw[j] = ld_node(ix.nodes, d[j] & SLOT_MASK, pol);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       if ((d[j] >> 30) == TAG_CHILD) {
-        const uint32_t sub = (((dy[j] >> s) & m) << NODE_K) | ((dx[j] >> s) & m);
-        d[j] = node_step(nw[j], sub);
+        if (d[j] & DESC_COMPACT) {  // compact leaf: answered here
+          const int32_t v = compact_answer(nw[j], ix.nodes, d[j] & SLOT_MASK,
+                                           ((d[j] >> DESC_SLOTS_SHIFT) & 3u) + 1u, qx[j], qy[j], pol);
+          d[j] = v < 0 ? make_desc(TAG_EMPTY, 0) : make_desc(TAG_INTERIOR, (uint32_t)v);
+        } else {
+          const uint32_t sub = (((dy[j] >> s) & m) << NODE_K) | ((dx[j] >> s) & m);
+          d[j] = node_step(nw[j], sub);
+        }
       }
     }
   }
@@ -225,7 +231,9 @@ struct TrieRing {
     count += __shfl_sync(full, incl, 31);
   }
 
-  // one trie level for the ring's first `take` entries (take <= 128, uniform)
+  // one trie level for the ring's first `take` entries (take <= 128,
+  // uniform); COMPACT = false for a trie without compact leaves
+  template <bool COMPACT = true>
   __device__ __forceinline__ void step(uint32_t take, const IndexView& ix, uint64_t pol,
                                        int32_t* __restrict__ out_base, uint32_t code_base,
                                        ChunkWriter& res, Residual* __restrict__ queue,
@@ -262,15 +270,42 @@ struct TrieRing {
     NodeWords nw[4];
     const uint64_t cold = policy_evict_first();
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      if ((have >> j) & 1u) nw[j] = ld_node(ix.nodes, d[j], d[j] < ix.hot_nodes ? pol : cold);
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t sl = d[j] & SLOT_MASK;
+      if ((have >> j) & 1u) nw[j] = ld_node(ix.nodes, sl, sl < ix.hot_nodes ? pol : cold);
+    }
     uint32_t leaf = 0, again = 0;
+    if (COMPACT) {  // compact leaves: answered here, one entry per pass of a
+                    // rolled loop (one copy of the evaluation keeps the code small)
+      uint32_t cm = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) cm |= (((have >> j) & 1u) && (d[j] & DESC_COMPACT) ? 1u : 0u) << j;
+      have &= ~cm;
+#pragma unroll 1
+      while (cm) {
+        const int j = __ffs(cm) - 1;
+        cm &= cm - 1;
+        uint32_t w[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          w[k] = j == 0 ? nw[0].w[k] : j == 1 ? nw[1].w[k] : j == 2 ? nw[2].w[k] : nw[3].w[k];
+        const uint32_t dj = j == 0 ? d[0] : j == 1 ? d[1] : j == 2 ? d[2] : d[3];
+        const int32_t px = j == 0 ? qx[0] : j == 1 ? qx[1] : j == 2 ? qx[2] : qx[3];
+        const int32_t py = j == 0 ? qy[0] : j == 1 ? qy[1] : j == 2 ? qy[2] : qy[3];
+        const uint32_t zj = j == 0 ? z[0] : j == 1 ? z[1] : j == 2 ? z[2] : z[3];
+        const uint32_t sl = dj & SLOT_MASK;
+        const int32_t v = compact_answer_words(w[0], w[1], w[2], w[3], w[4], w[5], w[6], w[7], ix.nodes, sl,
+                                               ((dj >> DESC_SLOTS_SHIFT) & 3u) + 1u, px, py,
+                                               sl < ix.hot_nodes ? pol : cold);
+        if (v >= 0) out_base[zj] = v;
+      }
+    }
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       if ((have >> j) & 1u) {
         const uint32_t dx = (uint32_t)qx[j] - (uint32_t)ix.gx0, dy = (uint32_t)qy[j] - (uint32_t)ix.gy0;
         const uint32_t sub = (((dy >> sh[j]) & m) << NODE_K) | ((dx >> sh[j]) & m);
-        d[j] = node_step(nw[j], sub);
+        d[j] = node_step<COMPACT>(nw[j], sub);
         const uint32_t tag = d[j] >> 30;
         if (tag == TAG_INTERIOR) out_base[z[j]] = (int32_t)(d[j] & PAYLOAD_MASK);
         if (tag == TAG_LEAF && ix.approx_id) {  // approximate mode: the leaf's own answer

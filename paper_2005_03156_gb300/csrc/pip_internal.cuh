@@ -22,6 +22,23 @@
 //                                   with ay == by is horizontal and never
 //                                   counts (kept only to mark the boundary)
 //   sbdesc uint2 per superbin: blob offset and size in 16-byte units.
+//
+// Compact leaves. A boundary cell whose kept candidates (at most 3) share at
+// most a few distinct non-horizontal edges is answered in the classify
+// kernel itself from one record of 1..4 consecutive 32-byte slots of the
+// node array (no residual queue, no binning):
+//   w[0]      E (bits 0-2: distinct edges) | C << 3 (bits 3-4: candidates)
+//   w[1..3]   candidate words: id (bits 0-23) | edge mask << 24 (bits 24-30:
+//             which of the E edges belong to the candidate) | base << 31
+//   w[4..]    the E edges as int4 (ax, ay, bx, by), ay < by: edge 0 in
+//             slot 0 words 4-7, edges 1-2 in slot 1, 3-4 in slot 2, 5-6 in
+//             slot 3.
+// A point's answer is the first candidate whose base parity XOR the parity
+// of its counted edges is odd (the candidate lists keep id order), else -1.
+// A CHILD descriptor with DESC_COMPACT set names such a record: its slot in
+// bits 0-26 and the record's slot count minus one in bits 27-28. Inside a
+// trie node a compact child has both its leaf and its split bit set, takes
+// its slots in the child numbering, and keeps slots - 1 in its 2-bit code.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -44,6 +61,18 @@ constexpr int SB_LOG2 = 5;  // 32 leaf slots per superbin
 constexpr int SB_SLOTS = 1 << SB_LOG2;
 constexpr int BLOB_HEADER_WORDS = SB_SLOTS + 1;
 constexpr int MAX_LEVELS = 12;
+constexpr uint32_t DESC_COMPACT = 1u << 29;
+constexpr int DESC_SLOTS_SHIFT = 27;
+constexpr uint32_t SLOT_MASK = (1u << 27) - 1u;  // node-array slots (32 bytes each)
+constexpr int COMPACT_MAX_EDGES = 7;
+constexpr int COMPACT_MAX_CANDS = 3;
+constexpr uint32_t CAND_ID_MASK = (1u << 24) - 1u;
+
+// Slots of a compact record with E distinct edges: edge 0 shares slot 0
+// with the header and candidates, later edges take two per slot.
+__host__ __device__ inline uint32_t compact_slots_for(uint32_t edges) {
+  return edges <= 1u ? 1u : 1u + (edges) / 2u;
+}
 
 __host__ __device__ inline uint32_t make_desc(uint32_t tag, uint32_t payload) {
   return (tag << 30) | (payload & PAYLOAD_MASK);
@@ -66,9 +95,10 @@ struct IndexView {
   int32_t gx0, gy0;       // lattice origin of the grid
   uint32_t nx, ny;        // top cells per row / column
   int32_t s0;             // log2 side of a top cell
-  int32_t depth;          // deepest level present
+  int32_t depth;          // deepest level present (trie levels below the top grid)
   uint32_t n_sb;          // superbins
   uint32_t hot_nodes;     // nodes [0, hot_nodes) (the shallow levels) are kept in L2
+  uint32_t compact;       // 1: the trie holds compact leaves (see above)
   const uint32_t* table;  // top-grid descriptors
   const uint4* nodes;     // trie nodes, two uint4 per node
   const uint4* blobs;     // superbin records (16-byte units)
@@ -121,13 +151,40 @@ __device__ __forceinline__ NodeWords ld_node(const uint4* nodes, uint32_t node, 
   return n;
 }
 
+// Bit j of a 16-bit mask to bits 2j and 2j+1.
+__device__ __forceinline__ uint32_t spread2(uint32_t m) {
+  m = (m | (m << 8)) & 0x00FF00FFu;
+  m = (m | (m << 4)) & 0x0F0F0F0Fu;
+  m = (m | (m << 2)) & 0x33333333u;
+  m = (m | (m << 1)) & 0x55555555u;
+  return m | (m << 1);
+}
+
 // One trie step: child `sub` of node n. Returns a descriptor; TAG_CHILD
-// means descend into node `payload`.
+// means descend into node `payload`, or, with DESC_COMPACT set, answer from
+// the compact record at that slot. Split children and compact children
+// share the child numbering; a compact child takes (its code + 1) slots.
+// COMPACT = false is the same step for a trie without compact children.
+template <bool COMPACT = true>
 __device__ __forceinline__ uint32_t node_step(const NodeWords& n, uint32_t sub) {
   const uint32_t bit = 1u << sub, below = bit - 1u;
   const uint32_t lm = n.w[0] & 0xFFFFu, cm = n.w[0] >> 16;
-  if (lm & bit) return make_desc(TAG_LEAF, n.w[2] + __popc(lm & below));
-  if (cm & bit) return make_desc(TAG_CHILD, n.w[3] + __popc(cm & below));
+  if (!COMPACT) {
+    if (lm & bit) return make_desc(TAG_LEAF, n.w[2] + __popc(lm & below));
+    if (cm & bit) return make_desc(TAG_CHILD, n.w[3] + __popc(cm & below));
+  }
+  const uint32_t both = lm & cm;
+  if (COMPACT && ((lm | cm) & bit)) {
+    if ((lm & bit) && !(cm & bit)) return make_desc(TAG_LEAF, n.w[2] + __popc(lm & ~cm & below));
+    uint32_t slot = n.w[3] + __popc(cm & below);
+    if (both & below) {  // compact children before this one take (code + 1) slots each
+      const uint32_t v = n.w[1] & spread2(both & below);
+      slot += __popc(v & 0x55555555u) + 2u * __popc(v & 0xAAAAAAAAu);
+    }
+    if (!(both & bit)) return make_desc(TAG_CHILD, slot);
+    const uint32_t extra = (n.w[1] >> (2 * sub)) & 3u;
+    return make_desc(TAG_CHILD, DESC_COMPACT | (extra << DESC_SLOTS_SHIFT) | slot);
+  }
   const uint32_t code = (n.w[1] >> (2 * sub)) & 3u;
   const int32_t id = (int32_t)(code == 0 ? n.w[4] : code == 1 ? n.w[5] : code == 2 ? n.w[6] : n.w[7]);
   return id < 0 ? make_desc(TAG_EMPTY, 0) : make_desc(TAG_INTERIOR, (uint32_t)id);
@@ -227,6 +284,42 @@ __device__ __forceinline__ uint32_t edge_crosses(int4 e, int32_t px, int32_t py)
   const long long l = (long long)sub32(e.z, e.x) * (long long)sub32(py, e.y);
   const long long r = (long long)sub32(e.w, e.y) * (long long)sub32(px, e.x);
   return (uint32_t)(in_y & (right | (span & (l > r))));
+}
+
+// Answer of a compact leaf for the lattice point (px, py): w0..w7 are the
+// record's first slot (already loaded); the other slots, slot + 1 .. slot +
+// nslots - 1, are loaded here. Edge k's crossing goes to bit k of a mask;
+// candidate i is inside iff its base XOR the parity of (mask AND its own
+// edge mask) is odd (Sec. III-A, restricted to the cell's kept edges).
+__device__ __forceinline__ int32_t compact_answer_words(uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3,
+                                                     uint32_t w4, uint32_t w5, uint32_t w6, uint32_t w7,
+                                                     const uint4* nodes, uint32_t slot, uint32_t nslots,
+                                                     int32_t px, int32_t py, uint64_t pol) {
+  const uint32_t ne = w0 & 7u, nc = (w0 >> 3) & 3u;
+  uint32_t cross = 0;
+  if (ne > 0u) cross = edge_crosses(make_int4((int)w4, (int)w5, (int)w6, (int)w7), px, py);
+#pragma unroll 1
+  for (uint32_t k = 1; k < nslots; ++k) {
+    const NodeWords b = ld_node(nodes, slot + k, pol);
+    if (2 * k - 1 < ne)
+      cross |= edge_crosses(make_int4((int)b.w[0], (int)b.w[1], (int)b.w[2], (int)b.w[3]), px, py) << (2 * k - 1);
+    if (2 * k < ne)
+      cross |= edge_crosses(make_int4((int)b.w[4], (int)b.w[5], (int)b.w[6], (int)b.w[7]), px, py) << (2 * k);
+  }
+  int32_t id = -1;
+  const uint32_t cw[3] = {w1, w2, w3};
+#pragma unroll
+  for (uint32_t i = 0; i < 3; ++i) {
+    const uint32_t par = (cw[i] >> 31) ^ (__popc((cw[i] >> 24) & 0x7Fu & cross) & 1u);
+    if (id < 0 && i < nc && par) id = (int32_t)(cw[i] & CAND_ID_MASK);
+  }
+  return id;
+}
+
+__device__ __forceinline__ int32_t compact_answer(const NodeWords& a, const uint4* nodes, uint32_t slot,
+                                                  uint32_t nslots, int32_t px, int32_t py, uint64_t pol) {
+  return compact_answer_words(a.w[0], a.w[1], a.w[2], a.w[3], a.w[4], a.w[5], a.w[6], a.w[7], nodes, slot,
+                              nslots, px, py, pol);
 }
 
 // ---------------------------------------------------------------------------

@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(K1_THREADS, 3) k_classify_points(
 // larger carve-out measurably throttles them.
 constexpr int DQ_THREADS = 128;
 
-template <bool VEC>
+template <bool VEC, bool COMPACT>
 __global__ void __launch_bounds__(DQ_THREADS, 5) k_classify_dq(
     IndexView ix, const double* __restrict__ lon, const double* __restrict__ lat, int64_t n,
     int32_t* __restrict__ out, Residual* __restrict__ queue, uint32_t* __restrict__ qcount,
@@ -158,10 +158,11 @@ __global__ void __launch_bounds__(DQ_THREADS, 5) k_classify_dq(
       res.put(leaf, qx, qy, d, [&](int j) { return idx[j]; }, queue, qcount, hist, 0u);
     if (__any_sync(full, split != 0u)) tr.push(split, qx, qy, idx, d, sh);
 #pragma unroll 1
-    while (tr.count >= 128u) tr.step(128u, ix, pol, out, 0u, res, queue, qcount, hist, 0u);
+    while (tr.count >= 128u) tr.step<COMPACT>(128u, ix, pol, out, 0u, res, queue, qcount, hist, 0u);
   }
 #pragma unroll 1
-  while (tr.count > 0u) tr.step(tr.count < 128u ? tr.count : 128u, ix, pol, out, 0u, res, queue, qcount, hist, 0u);
+  while (tr.count > 0u)
+    tr.step<COMPACT>(tr.count < 128u ? tr.count : 128u, ix, pol, out, 0u, res, queue, qcount, hist, 0u);
   res.finish(queue, qcount + 2);
 }
 
@@ -375,7 +376,7 @@ static unsigned k1_grid(int64_t n) {
   static std::atomic<int> occ_cache{0};
   int occ = occ_cache.load(std::memory_order_relaxed);
   if (!occ) {
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_classify_dq<true>, DQ_THREADS, 0) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_classify_dq<true, true>, DQ_THREADS, 0) != cudaSuccess)
       occ = 1;
     occ = std::max(1, occ);
     occ_cache.store(occ, std::memory_order_relaxed);
@@ -398,10 +399,14 @@ cudaError_t k1_launch(const IndexView& ix, const double* lon, const double* lat,
                       int32_t* out, Residual* queue, uint32_t* qcount, uint32_t* hist, cudaStream_t s) {
   const bool vec = ((uintptr_t)lon % 16 == 0) && ((uintptr_t)lat % 16 == 0) && ((uintptr_t)out % 16 == 0);
   const unsigned g1 = k1_grid(n);
-  if (vec)
-    k_classify_dq<true><<<g1, DQ_THREADS, 0, s>>>(ix, lon, lat, n, out, queue, qcount, hist);
+  if (vec && ix.compact)
+    k_classify_dq<true, true><<<g1, DQ_THREADS, 0, s>>>(ix, lon, lat, n, out, queue, qcount, hist);
+  else if (vec)
+    k_classify_dq<true, false><<<g1, DQ_THREADS, 0, s>>>(ix, lon, lat, n, out, queue, qcount, hist);
+  else if (ix.compact)
+    k_classify_dq<false, true><<<g1, DQ_THREADS, 0, s>>>(ix, lon, lat, n, out, queue, qcount, hist);
   else
-    k_classify_dq<false><<<g1, DQ_THREADS, 0, s>>>(ix, lon, lat, n, out, queue, qcount, hist);
+    k_classify_dq<false, false><<<g1, DQ_THREADS, 0, s>>>(ix, lon, lat, n, out, queue, qcount, hist);
   return cudaGetLastError();
 }
 

@@ -11,7 +11,11 @@
 // plan and copies the ids back. Requests that arrive while launches are in
 // flight wait only for the next free slot, so their work overlaps the
 // running launches (continuous batching). A host callback on the stream
-// marks the requests done and records their latency.
+// marks the requests done and records their latency. A request larger than
+// one launch holds is queued as consecutive parts of at most a launch each
+// (its point vector cut into ranges, Appendix A takes vectors of any
+// length); its ticket completes, and its latency is recorded, when the last
+// part is done.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -43,7 +47,25 @@ struct Req {
   pip_status err = PIP_OK;
   int64_t off = 0;       // offset in the slot's staging buffers
   bool gathered = false;
+  Req* parent = nullptr;                  // a part of a split request: the whole request
+  int64_t parts_left = 0;                 // whole split request: parts not done yet
+  std::vector<std::unique_ptr<Req>> parts;
 };
+
+// Mark r done (lock held); returns the request whose latency completes now,
+// or nullptr while parts of a split request are still outstanding.
+Req* finish_req(Req* r, Clock::time_point now, pip_status err) {
+  r->t_done = now;
+  r->state = 2;
+  if (err != PIP_OK) r->err = err;
+  Req* p = r->parent;
+  if (!p) return r;
+  if (err != PIP_OK) p->err = err;
+  if (--p->parts_left > 0) return nullptr;
+  p->t_done = now;
+  p->state = 2;
+  return p;
+}
 
 struct Slot;
 
@@ -101,10 +123,10 @@ void CUDART_CB slot_done(void* arg) {
   pip_server_s* S = sl->srv;
   const auto now = Clock::now();
   std::lock_guard<std::mutex> lk(S->mu);
-  for (Req* r : sl->batch) {
-    if (r->gathered && r->n > 0) std::memcpy(r->out, sl->hout + r->off, r->n * sizeof(int32_t));
-    r->t_done = now;
-    r->state = 2;
+  for (Req* part : sl->batch) {
+    if (part->gathered && part->n > 0) std::memcpy(part->out, sl->hout + part->off, part->n * sizeof(int32_t));
+    Req* r = finish_req(part, now, PIP_OK);
+    if (!r) continue;
     const double us = std::chrono::duration<double, std::micro>(r->t_done - r->t_sub).count();
     if ((int64_t)S->lat_us.size() < LAT_WINDOW) S->lat_us.push_back(us);
     else S->lat_us[S->lat_seen % LAT_WINDOW] = us;
@@ -195,11 +217,7 @@ void dispatch_loop(pip_server_s* S) {
     pip_status st = launch_batch(S, free_slot);
     lk.lock();
     if (st != PIP_OK) {  // fail the batch's requests; the slot stays usable
-      for (Req* r : free_slot->batch) {
-        r->err = st;
-        r->state = 2;
-        r->t_done = Clock::now();
-      }
+      for (Req* r : free_slot->batch) finish_req(r, Clock::now(), st);
       free_slot->batch.clear();
       free_slot->busy = false;
       S->cv.notify_all();
@@ -262,11 +280,11 @@ extern "C" pip_status pip_server_submit(pip_server srv, int32_t set, const doubl
   if (!srv || !ticket) return fail(PIP_EINVAL, "pip_server_submit: NULL argument");
   if (set < 0 || set >= (int32_t)srv->sets.size()) return fail(PIP_EINVAL, "pip_server_submit: bad set");
   if (n < 0 || (n > 0 && (!lon || !lat || !out))) return fail(PIP_EINVAL, "pip_server_submit: bad buffers");
-  if (n > srv->cap_points)
-    return fail(PIP_EINVAL, "pip_server_submit: request larger than a launch (max_batch_points)");
+  const int64_t cap = srv->cap_points;
+  const int64_t n_parts = n > cap ? (n + cap - 1) / cap : 1;
   std::lock_guard<std::mutex> lk(srv->mu);
   if (srv->stop) return fail(PIP_EINVAL, "pip_server_submit: server is stopping");
-  if ((int64_t)srv->pending.size() >= srv->opts.max_pending) {
+  if ((int64_t)srv->pending.size() + n_parts > srv->opts.max_pending) {
     ++srv->rejected;
     return fail(PIP_EBUSY, "pip_server_submit: queue full");
   }
@@ -279,7 +297,25 @@ extern "C" pip_status pip_server_submit(pip_server srv, int32_t set, const doubl
   r->out = out;
   r->t_sub = Clock::now();
   *ticket = r->ticket;
-  srv->pending.push_back(r.get());
+  if (n_parts == 1) {
+    srv->pending.push_back(r.get());
+  } else {  // consecutive ranges of at most one launch each
+    r->parts_left = n_parts;
+    for (int64_t k = 0; k < n_parts; ++k) {
+      auto q = std::make_unique<Req>();
+      const int64_t a = k * cap, m = std::min(cap, n - a);
+      q->ticket = r->ticket;
+      q->set = set;
+      q->lon = lon + a;
+      q->lat = lat + a;
+      q->n = m;
+      q->out = out + a;
+      q->t_sub = r->t_sub;
+      q->parent = r.get();
+      srv->pending.push_back(q.get());
+      r->parts.push_back(std::move(q));
+    }
+  }
   srv->reqs.emplace(r->ticket, std::move(r));
   ++srv->submitted;
   srv->cv.notify_all();

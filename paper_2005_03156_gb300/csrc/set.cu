@@ -249,3 +249,51 @@ extern "C" pip_status pip_parent_ids(pip_set set, const int32_t* ids, int64_t n,
   count_launches(1);
   return PIP_OK;
 }
+
+// Which cell of the index answers each lattice point (Sec. IV: interior
+// cells answer without a test; boundary cells keep the crossing test). The
+// walk is the one the classify kernels take.
+__global__ void k_locate(IndexView ix, const int32_t* __restrict__ qx, const int32_t* __restrict__ qy,
+                         int64_t n, uint32_t* __restrict__ code) {
+  const uint32_t m = (1u << NODE_K) - 1u;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t x = qx[i], y = qy[i];
+    const uint32_t dx = (uint32_t)x - (uint32_t)ix.gx0, dy = (uint32_t)y - (uint32_t)ix.gy0;
+    const uint32_t cx = dx >> ix.s0, cy = dy >> ix.s0;
+    if (x < ix.gx0 || y < ix.gy0 || cx >= ix.nx || cy >= ix.ny) {
+      code[i] = PIP_LOC_OUTSIDE;
+      continue;
+    }
+    uint32_t d = ix.table[(size_t)cy * ix.nx + cx];
+    uint32_t depth = 0;
+    int s = ix.s0;
+    while ((d >> 30) == TAG_CHILD && !(d & DESC_COMPACT)) {
+      s -= NODE_K;
+      const uint32_t* w = reinterpret_cast<const uint32_t*>(ix.nodes + 2 * (size_t)(d & SLOT_MASK));
+      NodeWords nw;
+      for (int k = 0; k < 8; ++k) nw.w[k] = w[k];
+      d = node_step<true>(nw, (((dy >> s) & m) << NODE_K) | ((dx >> s) & m));
+      ++depth;
+    }
+    const uint32_t tag = d >> 30;
+    const uint32_t kind = tag == TAG_EMPTY ? PIP_LOC_EMPTY
+                        : tag == TAG_INTERIOR ? PIP_LOC_INTERIOR
+                        : tag == TAG_LEAF ? PIP_LOC_RESIDUAL : PIP_LOC_COMPACT;
+    code[i] = kind | (depth << 8);
+  }
+}
+
+extern "C" pip_status pip_locate(pip_set set, const int32_t* qx, const int32_t* qy, int64_t n, uint32_t* code,
+                                 void* stream) {
+  if (!set) return fail(PIP_EINVAL, "pip_locate: NULL set");
+  if (n < 0) return fail(PIP_EINVAL, "pip_locate: n < 0");
+  if (n == 0) return PIP_OK;
+  if (!qx || !qy || !code || !is_device_ptr(qx) || !is_device_ptr(qy) || !is_device_ptr(code))
+    return fail(PIP_EINVAL, "pip_locate: qx, qy and code must be device memory");
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, num_sms() * 8));
+  k_locate<<<g, 256, 0, (cudaStream_t)stream>>>(set->view, qx, qy, n, code);
+  PIP_CUDA(cudaGetLastError());
+  count_launches(1);
+  return PIP_OK;
+}

@@ -190,21 +190,24 @@ class NationalPoints:
         return lon, lat
 
 
-def batched_sets(seed=SEEDS["batched"], n_sets=8, lo=10_000, hi=200_000, scale=1.0):
-    """8 sets with log-spaced block counts and vertex medians 6..40."""
+def batched_set(s, seed=SEEDS["batched"], n_sets=8, lo=10_000, hi=200_000, scale=1.0):
+    """Set s of the batched workload: log-spaced block counts and vertex
+    medians 6..40 over the n_sets sets."""
     sizes = np.rint(np.geomspace(lo, hi, n_sets) * scale).astype(np.int64)
     medians = np.rint(np.geomspace(6, 40, n_sets)).astype(np.int64)
-    out = []
-    for s in range(n_sets):
-        deg = float(np.sqrt(sizes[s] / 8000.0))  # ~8,000 blocks per square degree
-        box_deg = (-100.0 + 12 * s, 30.0, -100.0 + 12 * s + deg, 30.0 + deg)
-        mix = Mixture(_box_units(box_deg), _rng(seed, 300 + s))
-        pset = _state_like(_rng(seed, 400 + s), _box_units(box_deg), int(sizes[s]), mix,
-                           vert_median=int(medians[s]), n_tracts=max(4, int(sizes[s]) // 40),
-                           n_counties=max(2, int(sizes[s]) // 5000), n_forced=1)
-        pset.meta.update(config="batched", set=s, mixture=mix)
-        out.append(pset)
-    return out
+    deg = float(np.sqrt(sizes[s] / 8000.0))  # ~8,000 blocks per square degree
+    box_deg = (-100.0 + 12 * s, 30.0, -100.0 + 12 * s + deg, 30.0 + deg)
+    mix = Mixture(_box_units(box_deg), _rng(seed, 300 + s))
+    pset = _state_like(_rng(seed, 400 + s), _box_units(box_deg), int(sizes[s]), mix,
+                       vert_median=int(medians[s]), n_tracts=max(4, int(sizes[s]) // 40),
+                       n_counties=max(2, int(sizes[s]) // 5000), n_forced=1)
+    pset.meta.update(config="batched", set=s, mixture=mix)
+    return pset
+
+
+def batched_sets(seed=SEEDS["batched"], n_sets=8, lo=10_000, hi=200_000, scale=1.0):
+    """8 sets with log-spaced block counts and vertex medians 6..40."""
+    return [batched_set(s, seed, n_sets, lo, hi, scale) for s in range(n_sets)]
 
 
 def batched_query_sizes(seed=SEEDS["batched"], n_queries=4096, lo=100, hi=1_000_000,

@@ -23,3 +23,10 @@ def tiny_set():
 def tiny_set_holes():
     from synth import configs
     return configs.tiny_set(seed=11, n_blocks=400, holes=0.1)
+
+
+@pytest.fixture(scope="session")
+def state_set():
+    """The state-scale set (199,972 blocks); about 20 s to generate."""
+    from synth import configs
+    return configs.state_set()

@@ -1,0 +1,137 @@
+"""Parity at the full sizes of the state, batched and national workloads, in
+the launch shapes bench.py times. The oracle checks bounded samples of the
+outputs point by point (ids are integers: bit-exact), and every output must
+be a valid id. The samples include the degenerate points the tie rule has to
+settle: vertices, lattice points on edges and points one unit around
+vertices, over the whole set and over its hardest polygons."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle
+from synth import configs, degenerate_lattice, lattice_to_degrees
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def pipm():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2005_03156_gb300 as pipm
+    from paper_2005_03156_gb300 import build
+    build.build()
+    pipm.lib()
+    return pipm
+
+
+def polygon_vertices(ps, p, ring=None):
+    """Vertex index range of polygon p (all rings, or ring number `ring` of p)."""
+    r0, r1 = ps.poly_ring_off[p], ps.poly_ring_off[p + 1]
+    if ring is not None:
+        r0, r1 = r0 + ring, r0 + ring + 1
+    return np.arange(ps.ring_off[r0], ps.ring_off[r1])
+
+
+def around(qx, qy):
+    """Each point and its four lattice neighbours."""
+    dx = np.array([0, 1, -1, 0, 0])
+    dy = np.array([0, 0, 0, 1, -1])
+    return (qx[:, None] + dx).ravel(), (qy[:, None] + dy).ravel()
+
+
+@pytest.mark.parametrize("opts", [None, {"compact_edges": 3}], ids=["default", "compact"])
+def test_state_degenerate_points(pipm, state_set, opts):
+    """State-scale set (199,972 blocks, three 2,000-vertex blocks, 2 % holes
+    filled by islands) with its full index: 200,000 degenerate points over the
+    whole set, plus every vertex of the three largest blocks (up to 2,000
+    vertices) and of 300 hole rings with their four neighbours, against the
+    oracle; with the default index and with compact leaves."""
+    ps = state_set
+    rng = np.random.default_rng(80)
+    qx, qy = degenerate_lattice(ps, 200_000, rng)
+    nv = np.diff(ps.ring_off[ps.poly_ring_off])
+    big = np.argsort(nv)[-3:]
+    assert nv[big].max() >= 2000
+    holed = np.flatnonzero(np.diff(ps.poly_ring_off) > 1)
+    assert len(holed) > 300
+    vi = np.concatenate([polygon_vertices(ps, p) for p in big] +
+                        [polygon_vertices(ps, p, ring=1) for p in rng.choice(holed, 300, replace=False)])
+    bx, by = around(ps.vx[vi].astype(np.int64), ps.vy[vi].astype(np.int64))
+    qx, qy = np.concatenate([qx, bx]), np.concatenate([qy, by])
+    lon, lat = lattice_to_degrees(qx), lattice_to_degrees(qy)
+    want = oracle.join_hier(ps, lon, lat)
+    s = pipm.load_polygon_set(ps, opts=opts)
+    got = pipm.pip_project(s, torch.from_numpy(lon).cuda(), torch.from_numpy(lat).cuda())
+    pipm.pip_set_check(s)
+    got = got.cpu().numpy()
+    assert (got == want).all(), int((got != want).sum())
+    s.free()
+
+
+def test_batched_full_sets(pipm):
+    """The batched workload's 8 sets (10,020..199,952 blocks, vertex medians
+    6..40) and its first 256 queries (lognormal sizes 100..1e6) in one
+    persistent graph launch, as bench.py builds them; every query's ids are
+    checked against the oracle on up to 20,000 sampled points."""
+    psets = configs.batched_sets()
+    sizes, _ = configs.batched_query_sizes()
+    rng = np.random.Generator(np.random.PCG64([configs.SEEDS["batched"], 600]))
+    set_of = rng.integers(0, len(psets), len(sizes))
+    sizes, set_of = sizes[:256], set_of[:256]
+    sets = [pipm.load_polygon_set(p) for p in psets]
+    qs, host = [], []
+    for i, n in enumerate(sizes):
+        k = int(set_of[i])
+        lon, lat = psets[k].meta["mixture"].sample_degrees(
+            int(n), np.random.Generator(np.random.PCG64([configs.SEEDS["batched"], 7000 + i])))
+        out = torch.full((int(n),), -7, dtype=torch.int32, device="cuda")
+        qs.append((sets[k], torch.from_numpy(lon).cuda(), torch.from_numpy(lat).cuda(), out))
+        host.append((k, lon, lat))
+    plan = pipm.Plan(max_points=int(sizes.sum()), max_queries=len(qs))
+    plan.run(qs)
+    plan.check()
+    torch.cuda.synchronize()
+    smp = np.random.default_rng(81)
+    for k in range(len(psets)):
+        mine = [i for i in range(len(qs)) if host[i][0] == k]
+        if not mine:
+            continue
+        picks = [np.sort(smp.choice(len(host[i][1]), min(20_000, len(host[i][1])), replace=False))
+                 for i in mine]
+        lon = np.concatenate([host[i][1][p] for i, p in zip(mine, picks)])
+        lat = np.concatenate([host[i][2][p] for i, p in zip(mine, picks)])
+        want = oracle.Hier(psets[k]).join(lon, lat)
+        at = 0
+        for i, p in zip(mine, picks):
+            got = qs[i][3].cpu().numpy()
+            assert got.min() >= -1 and got.max() < psets[k].n_poly, i
+            assert (got[p] == want[at:at + len(p)]).all(), (i, int((got[p] != want[at:at + len(p)]).sum()))
+            at += len(p)
+
+
+def test_national_chunk_streamed(pipm):
+    """The national set (799,959 blocks in 50 regions) and one 1e8-point
+    chunk of its stream projected from pinned host memory through the chunked
+    host pipeline, as bench.py's national mode runs it; 200,000 sampled
+    outputs against the oracle, plus degenerate points of the set."""
+    ps = configs.national_set()
+    s = pipm.load_polygon_set(ps)
+    lon, lat = configs.national_points_chunk(0, 100_000_000)
+    hl = torch.from_numpy(lon).pin_memory()
+    ha = torch.from_numpy(lat).pin_memory()
+    ho = torch.full((len(lon),), -7, dtype=torch.int32).pin_memory()
+    pipm.pip_project(s, hl, ha, ho)
+    pipm.pip_set_check(s)
+    got = ho.numpy()
+    assert got.min() >= -1 and got.max() < ps.n_poly
+    idx = np.random.default_rng(82).choice(len(lon), 200_000, replace=False)
+    want = oracle.join_hier(ps, lon[idx], lat[idx])
+    assert (got[idx] == want).all(), int((got[idx] != want).sum())
+    qx, qy = degenerate_lattice(ps, 100_000, np.random.default_rng(83))
+    dlon, dlat = lattice_to_degrees(qx), lattice_to_degrees(qy)
+    got = pipm.pip_project(s, torch.from_numpy(dlon).cuda(), torch.from_numpy(dlat).cuda()).cpu().numpy()
+    want = oracle.join_hier(ps, dlon, dlat)
+    assert (got == want).all(), int((got != want).sum())
+    s.free()

@@ -90,7 +90,14 @@ OPTION_CASES = [
     dict(stage_depth=2, pts_per_cta=1000),               # items larger than the CTA
     dict(stage_depth=-1, pts_per_cta=300),               # no staging
     dict(cand_mode=2),                                   # box rasterization
-    dict(cand_mode=1, size_ratio=-1, leaf_edges=1000),   # few splits, long lists (warp ballots)
+    dict(cand_mode=1, size_ratio=-1, leaf_edges=1000, compact_edges=-1),  # long lists (warp ballots)
+    dict(compact_edges=-1),                              # no compact leaves: every leaf is residual
+    dict(leaf_edges=2, size_ratio=64, compact_edges=-1),  # deep trie, palette overflows become leaves
+    dict(compact_edges=1),                               # one-slot records only
+    dict(compact_edges=7),                               # records of up to four slots
+    dict(compact_edges=2, max_depth=1),                  # compact records beside residual leaves
+    dict(compact_edges=7, cell_log2=21, max_depth=8),    # coarse top grid, compact deep down
+    dict(compact_edges=3, max_depth=-1, cell_log2=15),   # uniform grid of compact cells
 ]
 
 
@@ -105,6 +112,33 @@ def test_build_options(pipm, tiny_set_holes, opts):
     got = project(pipm, s, lon, lat)
     want = oracle.join_hier(ps, lon, lat)
     assert (got == want).all(), (opts, int((got != want).sum()))
+
+
+def test_compact_leaves_answer_in_the_classify_kernel(pipm, tiny_set_holes):
+    """Compact leaves (boundary cells with few distinct edges, answered by the
+    exact crossing test inside K1): results equal the oracle and the index
+    without compact leaves, and almost no point is left for the residual
+    crossing kernel."""
+    ps = tiny_set_holes
+    qx, qy = degenerate_lattice(ps, 60_000, np.random.default_rng(26))
+    lon, lat = lattice_to_degrees(qx), lattice_to_degrees(qy)
+    lon2, lat2 = configs.tiny_points(ps, n=200_000, seed=27)
+    lon, lat = np.concatenate([lon, lon2]), np.concatenate([lat, lat2])
+    want = oracle.join_hier(ps, lon, lat)
+    res = {}
+    for ce in (3, -1):
+        s = pipm.load_polygon_set(ps, opts={"compact_edges": ce})
+        out, stats = pipm.pip_project_ex(s, dev(lon), dev(lat))
+        pipm.pip_set_check(s)
+        got = out.cpu().numpy()
+        assert (got == want).all(), (ce, int((got != want).sum()))
+        res[ce] = (s.info(), stats["residual"])
+    info_on, residual_on = res[3]
+    info_off, residual_off = res[-1]
+    assert info_on["compact_leaves"] > 0 and sum(info_on["compact_by_edges"]) == info_on["compact_leaves"]
+    assert info_on["compact_by_edges"][4:] == [0, 0, 0, 0]  # at most 3 edges
+    assert info_off["compact_leaves"] == 0
+    assert residual_on * 10 < residual_off
 
 
 def test_hierarchy_descent_equals_rasterization(pipm, tiny_set):
@@ -250,8 +284,9 @@ def kd_rectangles(rng, box, n):
     return [[[(a, b), (c, b), (c, d), (a, d)]] for a, b, c, d in rects]
 
 
-@pytest.mark.parametrize("opts", [None, dict(leaf_edges=1, size_ratio=64), dict(max_depth=-1),
-                                  dict(cell_log2=12, max_depth=5)])
+@pytest.mark.parametrize("opts", [None, dict(leaf_edges=1, size_ratio=64, compact_edges=-1),
+                                  dict(max_depth=-1), dict(cell_log2=12, max_depth=5),
+                                  dict(compact_edges=7, cell_log2=12, max_depth=5)])
 def test_axis_aligned_partition(pipm, opts):
     rng = np.random.default_rng(50)
     box = (1000, 2000, 1000 + 40_000, 2000 + 30_000)
@@ -272,7 +307,8 @@ def test_parent_ids_follow_the_hierarchy(pipm, tiny_set):
     s = pipm.load_polygon_set(tiny_set)
     lon, lat = configs.tiny_points(tiny_set, n=50_000, seed=55)
     ids = pipm.pip_project(s, dev(lon), dev(lat))
-    want = ids.cpu().numpy()
+    want = oracle.join_hier(tiny_set, lon, lat)  # expected ancestors come from the oracle's ids
+    assert (ids.cpu().numpy() == want).all()
     for level, par in enumerate(tiny_set.parents, start=1):
         got = pipm.pip_parent_ids(s, ids, level).cpu().numpy()
         want = np.where(want >= 0, par[np.maximum(want, 0)], -1)

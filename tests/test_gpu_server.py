@@ -1,6 +1,6 @@
 """Served form: continuous batching over resident sets. Every request's ids
-must be the same served alone, served in a concurrent mix, and projected by
-the plain path (tolerance 0: ids are integers)."""
+must equal the CPU oracle's, served alone, served in a concurrent mix and
+projected by the plain path (tolerance 0: ids are integers)."""
 import threading
 import time
 
@@ -9,6 +9,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle
 from synth import configs, degenerate_lattice, lattice_to_degrees
 
 pytestmark = pytest.mark.gpu
@@ -48,6 +49,11 @@ def requests(ps_list, rng, sizes):
     return reqs
 
 
+def oracle_ids(ps_list, reqs):
+    return [oracle.join_hier(ps_list[k], lon.numpy(), lat.numpy()) if len(lon) else np.zeros(0, np.int32)
+            for k, lon, lat, _ in reqs]
+
+
 def plain(pipm, sets, reqs):
     res = []
     for k, lon, lat, out in reqs:
@@ -64,7 +70,9 @@ def test_alone_equals_mix_equals_plain(pipm, resident):
     rng = np.random.default_rng(70)
     sizes = [0, 1, 2, 31, 1000, 40000, 100_000] + list((10 ** rng.uniform(0, 5, 120)).astype(int))
     reqs = requests(ps_list, rng, sizes)
-    want = plain(pipm, sets, reqs)
+    want = oracle_ids(ps_list, reqs)
+    for i, got in enumerate(plain(pipm, sets, reqs)):
+        assert (got == want[i]).all(), i
     srv = pipm.Server(sets, dict(n_streams=2, max_batch_queries=64))
     # alone: one request at a time
     alone = []
@@ -107,8 +115,6 @@ def test_server_limits(pipm, resident):
     srv = pipm.Server(sets, dict(n_streams=1, max_batch_points=1000, max_batch_queries=8))
     big = np.zeros(1001)
     out = np.zeros(1001, np.int32)
-    st, _ = srv.try_submit(0, big, big, out)
-    assert st == 1  # larger than one launch
     st, _ = srv.try_submit(5, big[:10], big[:10], out[:10])
     assert st == 1  # no such set
     t = srv.submit(0, big[:0], big[:0], out[:0])  # empty request completes
@@ -116,11 +122,44 @@ def test_server_limits(pipm, resident):
     srv.close()
 
 
+def test_request_larger_than_a_launch_is_split(pipm, resident):
+    """A request of about three launches (cap 1000 points) plus a ragged tail
+    is served in parts and its ticket completes once; small requests submitted
+    meanwhile from another thread are served alongside. Every id equals the
+    oracle's."""
+    ps_list, sets = resident
+    rng = np.random.default_rng(73)
+    big = requests(ps_list, rng, [3 * 1000 + 17, 2000, 1000])
+    small = requests(ps_list, rng, list((10 ** rng.uniform(0, 3, 40)).astype(int)))
+    want_big, want_small = oracle_ids(ps_list, big), oracle_ids(ps_list, small)
+    srv = pipm.Server(sets, dict(n_streams=2, max_batch_points=1000, max_batch_queries=8))
+    tickets = [None] * len(small)
+
+    def producer():
+        for i, (k, lon, lat, out) in enumerate(small):
+            tickets[i] = srv.submit(k, lon, lat, out)
+
+    th = threading.Thread(target=producer)
+    th.start()
+    big_t = [srv.submit(k, lon, lat, out) for k, lon, lat, out in big]
+    th.join()
+    for t in big_t + tickets:
+        srv.wait(t, timeout_us=60_000_000)
+    st = srv.stats()
+    srv.close()
+    for i, (k, lon, lat, out) in enumerate(big):
+        assert (out.numpy() == want_big[i]).all(), i
+    for i, (k, lon, lat, out) in enumerate(small):
+        assert (out.numpy() == want_small[i]).all(), i
+    assert st["completed"] == len(big) + len(small)  # one completion per ticket, not per part
+    assert st["launches"] >= 6
+
+
 def test_pageable_host_buffers(pipm, resident):
     ps_list, sets = resident
     rng = np.random.default_rng(71)
     reqs = requests(ps_list, rng, [5000, 70_000])
-    want = plain(pipm, sets, reqs)
+    want = oracle_ids(ps_list, reqs)
     srv = pipm.Server(sets, dict(n_streams=2))
     outs = []
     for k, lon, lat, out in reqs:
