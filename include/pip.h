@@ -122,8 +122,8 @@ typedef struct {
   int64_t superbins;        /* groups of 32 leaf slots, the binning key */
   int64_t leaf_cands;       /* candidate polygons over all leaves */
   int64_t leaf_edges;       /* clipped edges over all leaves */
-  int64_t index_bytes;      /* device bytes of table + leaf blobs */
-  int64_t max_blob_bytes;   /* largest per-superbin blob */
+  int64_t index_bytes;      /* device bytes of top grid, trie nodes, leaf records and their offsets */
+  int64_t max_blob_bytes;   /* largest superbin: the records of 32 consecutive leaf slots */
   int32_t cell_log2, fanout_log2, depth, cand_mode;
   int32_t pts_per_cta, stage_depth;
   int32_t grid_x0, grid_y0; /* lattice origin of the grid */

@@ -128,24 +128,22 @@ __device__ __forceinline__ void batch_test_chunk(const DevSet* sets, uint32_t n_
     if (active) {
       r = binned[first + t];
       const DevSet& S = sets[set_of_slot(sets, n_sets, r.w)];
-      const uint2 sd = S.view.sbdesc[(r.w >> SB_LOG2) - S.sb_base];
-      bp = staged ? staged + (sd.x - region16) : S.view.blobs + sd.x;
+      const uint32_t off = S.view.slot_off[r.w - (S.sb_base << SB_LOG2)];
+      bp = staged ? staged + (off - region16) : S.view.blobs + off;
     }
-    BlobView b{nullptr, nullptr};
-    if (active) b = blob_view(bp);
-    const uint32_t local = r.w & (SB_SLOTS - 1);
-    const bool is_long = active && leaf_edges(b, local) > (uint32_t)LONG_LIST;
+    LeafRec b{nullptr, nullptr};
+    if (active) b = leaf_rec(bp);
+    const bool is_long = active && leaf_edges(b) > (uint32_t)LONG_LIST;
     int32_t id = -1;
-    if (active && !is_long) id = test_point(b, local, (int32_t)r.x, (int32_t)r.y);
+    if (active && !is_long) id = test_point(b, (int32_t)r.x, (int32_t)r.y);
     uint32_t lm = __ballot_sync(0xffffffffu, is_long);
     while (lm) {
       const int j = __ffs(lm) - 1;
       lm &= lm - 1;
       const int32_t px = (int32_t)__shfl_sync(0xffffffffu, r.x, j);
       const int32_t py = (int32_t)__shfl_sync(0xffffffffu, r.y, j);
-      const uint32_t lj = __shfl_sync(0xffffffffu, local, j);
       const unsigned long long pj = __shfl_sync(0xffffffffu, (unsigned long long)(uintptr_t)bp, j);
-      const int32_t v = test_point_warp(blob_view((const uint4*)(uintptr_t)pj), lj, px, py);
+      const int32_t v = test_point_warp(leaf_rec((const uint4*)(uintptr_t)pj), px, py);
       if (lane == j) id = v;
     }
     if (active) store(r, id);
@@ -360,14 +358,15 @@ __global__ void __launch_bounds__(B_THREADS, 3) k_batch(PlanBufs B) {
         const uint32_t sa = set_of_slot(s_sets, H.n_sets, ga), sb = set_of_slot(s_sets, H.n_sets, gb);
         if (sa == sb) {
           const DevSet& S = s_sets[sa];
-          const uint2 da = S.view.sbdesc[(ga >> SB_LOG2) - S.sb_base];
-          const uint2 db = S.view.sbdesc[(gb >> SB_LOG2) - S.sb_base];
-          const uint32_t len16 = db.x + db.y - da.x;
+          // whole superbins (binned order sorts superbins, not slots)
+          const uint32_t da = S.view.slot_off[((ga >> SB_LOG2) - S.sb_base) << SB_LOG2];
+          const uint32_t db = S.view.slot_off[((gb >> SB_LOG2) - S.sb_base + 1) << SB_LOG2];
+          const uint32_t len16 = db - da;
           if (len16 <= H.stage16) {
             fence_proxy_async();
-            bulk_load(stage_mem, S.view.blobs + da.x, len16 * 16u, &bar);
+            bulk_load(stage_mem, S.view.blobs + da, len16 * 16u, &bar);
             s_staged = 1;
-            s_region = da.x;
+            s_region = da;
           }
         }
       }

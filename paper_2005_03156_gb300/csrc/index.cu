@@ -762,78 +762,68 @@ __global__ void k_children(int64_t n_child, int k, Grid g, int child_shift,
   }
 }
 
-// Blob sizes per superbin of this level (16-byte units).
-__global__ void k_blob_size(int64_t n_sb, int64_t n_leaf, const uint32_t* __restrict__ leaf_cell,
-                            const uint32_t* __restrict__ fc_nk, const uint32_t* __restrict__ fc_ne,
-                            uint64_t* __restrict__ size16) {
-  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n_sb;
-       b += (int64_t)gridDim.x * blockDim.x) {
-    uint64_t nc = 0, ne = 0;
-    for (int j = 0; j < SB_SLOTS; ++j) {
-      const int64_t l = b * SB_SLOTS + j;
-      if (l >= n_leaf) break;
-      const uint32_t c = leaf_cell[l];
-      nc += fc_nk[c];
-      ne += fc_ne[c];
+// Record size of every leaf slot of this level (16-byte units): header
+// (nc, candidates, edge ends) padded to 16 bytes, then the edges; padding
+// slots past the level's leaves get an empty one-unit record.
+__global__ void k_rec_size(int64_t n_slots, int64_t n_leaf, const uint32_t* __restrict__ leaf_cell,
+                           const uint32_t* __restrict__ fc_nk, const uint32_t* __restrict__ fc_ne,
+                           uint64_t* __restrict__ size16) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_slots;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    if (t >= n_leaf) {
+      size16[t] = 1;
+      continue;
     }
-    const uint64_t words = BLOB_HEADER_WORDS + nc + nc + 1;
-    size16[b] = (words + 3) / 4 + ne;
+    const uint32_t c = leaf_cell[t];
+    size16[t] = (1ull + 2ull * fc_nk[c] + 3ull) / 4ull + fc_ne[c];
   }
 }
 
-// Fill the blobs (warp per superbin).
-__global__ void k_blob_fill(int64_t n_sb, int64_t n_leaf, const uint32_t* __restrict__ leaf_cell,
-                            const uint64_t* __restrict__ kc_off, const int32_t* __restrict__ kc_poly,
-                            const uint8_t* __restrict__ kc_base, const uint32_t* __restrict__ kc_cnt,
-                            const uint64_t* __restrict__ kc_eoff, const int4* __restrict__ kedges,
-                            const uint64_t* __restrict__ boff, const uint64_t* __restrict__ bsize,
-                            uint4* __restrict__ blobs, uint2* __restrict__ sbdesc, uint64_t base16) {
+// Largest superbin (32 consecutive records) in 16-byte units, for reports.
+__global__ void k_superbin_max(int64_t n_sb, const uint64_t* __restrict__ off16, unsigned long long* out) {
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < n_sb;
+       b += (int64_t)gridDim.x * blockDim.x)
+    atomicMax(out, (unsigned long long)(off16[(b + 1) * SB_SLOTS] - off16[b * SB_SLOTS]));
+}
+
+// Fill the leaf records (warp per slot) and the slots' global offsets.
+__global__ void k_rec_fill(int64_t n_slots, int64_t n_leaf, const uint32_t* __restrict__ leaf_cell,
+                           const uint64_t* __restrict__ kc_off, const int32_t* __restrict__ kc_poly,
+                           const uint8_t* __restrict__ kc_base, const uint32_t* __restrict__ kc_cnt,
+                           const uint64_t* __restrict__ kc_eoff, const int4* __restrict__ kedges,
+                           const uint64_t* __restrict__ off16, uint4* __restrict__ blobs,
+                           uint32_t* __restrict__ slot_off, uint64_t base16) {
   const int lane = threadIdx.x & 31;
   const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t b = (((int64_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; b < n_sb; b += warps) {
-    uint4* blob = blobs + boff[b];
-    uint32_t* words = (uint32_t*)blob;
-    // candidate and edge totals of the superbin's first slots
-    const int64_t l0 = b * SB_SLOTS;
-    const int64_t nl = (n_leaf - l0 < (int64_t)SB_SLOTS) ? (n_leaf - l0) : (int64_t)SB_SLOTS;
-    // candidate starts per slot (serial over 32 slots in lane 0)
-    uint32_t nc = 0;
-    if (lane == 0) {
-      for (int j = 0; j < SB_SLOTS; ++j) {
-        words[j] = nc;
-        if (j < nl) {
-          const uint32_t c = leaf_cell[l0 + j];
-          nc += (uint32_t)(kc_off[c + 1] - kc_off[c]);
-        }
-      }
-      words[SB_SLOTS] = nc;
+  for (int64_t t = (((int64_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; t < n_slots; t += warps) {
+    uint4* rec = blobs + off16[t];
+    uint32_t* w = (uint32_t*)rec;
+    if (lane == 0) slot_off[t] = (uint32_t)(base16 + off16[t]);
+    if (t >= n_leaf) {
+      if (lane < 4) w[lane] = 0u;
+      continue;
     }
-    nc = __shfl_sync(0xffffffffu, nc, 0);
-    uint32_t* cand = words + BLOB_HEADER_WORDS;
-    uint32_t* estart = cand + nc;
-    const uint64_t edge16 = (BLOB_HEADER_WORDS + nc + nc + 1 + 3) / 4;
-    int4* edges = (int4*)(blob + edge16);
-    // walk the slots; each slot's candidates are contiguous in kc arrays
-    uint32_t ci = 0, ei = 0;
-    for (int j = 0; j < nl; ++j) {
-      const uint32_t c = leaf_cell[l0 + j];
-      for (uint64_t i = kc_off[c]; i < kc_off[c + 1]; ++i) {
-        if (lane == 0) {
-          cand[ci] = (uint32_t)kc_poly[i] | ((uint32_t)kc_base[i] << 31);
-          estart[ci] = ei;
-        }
-        const uint32_t cnt = kc_cnt[i];
-        const uint64_t src = kc_eoff[i];
-        for (uint32_t t = lane; t < cnt; t += 32) edges[ei + t] = kedges[src + t];
-        ei += cnt;
-        ++ci;
-      }
-    }
+    const uint32_t c = leaf_cell[t];
+    const uint64_t k0 = kc_off[c];
+    const uint32_t nc = (uint32_t)(kc_off[c + 1] - k0);
+    const uint32_t head = (1u + 2u * nc + 3u) / 4u;
+    int4* edges = (int4*)(rec + head);
     if (lane == 0) {
-      estart[nc] = ei;
-      // zero the padding words between estart and the edges
-      for (uint64_t w = BLOB_HEADER_WORDS + nc + nc + 1; w < edge16 * 4; ++w) words[w] = 0;
-      sbdesc[b] = make_uint2((uint32_t)(base16 + boff[b]), (uint32_t)bsize[b]);
+      w[0] = nc;
+      uint32_t e = 0;
+      for (uint32_t i = 0; i < nc; ++i) {
+        w[1 + i] = (uint32_t)kc_poly[k0 + i] | ((uint32_t)kc_base[k0 + i] << 31);
+        e += kc_cnt[k0 + i];
+        w[1 + nc + i] = e;
+      }
+      for (uint32_t k = 1 + 2 * nc; k < 4 * head; ++k) w[k] = 0u;
+    }
+    uint32_t at = 0;
+    for (uint32_t i = 0; i < nc; ++i) {
+      const uint32_t cnt = kc_cnt[k0 + i];
+      const uint64_t src = kc_eoff[k0 + i];
+      for (uint32_t q = lane; q < cnt; q += 32) edges[at + q] = kedges[src + q];
+      at += cnt;
     }
   }
 }
@@ -926,13 +916,12 @@ __global__ void k_leaf_centers(int64_t n_leaf, const uint32_t* __restrict__ leaf
 // Approximate mode: the exact id of each leaf's centre, from the leaf's own
 // record (its kept edges decide every point of the cell, Sec. III-A test).
 __global__ void k_leaf_answer(int64_t n_slots, const int2* __restrict__ centre,
-                              const uint4* __restrict__ blobs, const uint2* __restrict__ sbdesc,
+                              const uint4* __restrict__ blobs, const uint32_t* __restrict__ slot_off,
                               int32_t* __restrict__ answer) {
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_slots;
        t += (int64_t)gridDim.x * blockDim.x) {
     const int2 p = centre[t];
-    const BlobView b = blob_view(blobs + sbdesc[t >> SB_LOG2].x);
-    answer[t] = test_point(b, (uint32_t)(t & (SB_SLOTS - 1)), p.x, p.y);  // padding slots: no candidates, -1
+    answer[t] = test_point(leaf_rec(blobs + slot_off[t]), p.x, p.y);  // padding slots: no candidates, -1
   }
 }
 
@@ -1123,7 +1112,7 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
   std::vector<DBuf<uint32_t>> desc_lv;   // descriptors of this level's table part
   std::vector<int64_t> desc_len;
   std::vector<DBuf<uint4>> blob_lv;
-  std::vector<DBuf<uint2>> sbd_lv;
+  std::vector<DBuf<uint32_t>> sbd_lv;  // per level: the leaf slots' record offsets
   std::vector<DBuf<int2>> cen_lv;  // approximate mode: leaf centres per level
   std::vector<int64_t> blob_len, sb_len;
   std::vector<DBuf<TrieNode>> node_lv;  // nodes of each level's split cells
@@ -1334,15 +1323,19 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
                                                        o.compact_edges, (uint32_t*)node_lv.back().p);
       PIP_CUDA(cudaGetLastError());
     }
-    // leaves of this level -> superbin blobs
+    // leaves of this level -> one record per slot (superbins of 32 slots)
     const int64_t n_sb = (n_leaf + SB_SLOTS - 1) / SB_SLOTS;
     if (n_sb > 0) {
-      DBuf<uint64_t> bsize, boff, tot;
-      ALLOC(bsize, n_sb);
-      ALLOC(boff, n_sb + 1);
+      const int64_t n_slots_sb = n_sb * SB_SLOTS;
+      DBuf<uint64_t> rsize, roff, tot;
+      DBuf<unsigned long long> sbmax;
+      ALLOC(rsize, n_slots_sb);
+      ALLOC(roff, n_slots_sb + 1);
       ALLOC(tot, 1);
-      k_blob_size<<<blocks_for(n_sb), TB, 0, s>>>(n_sb, n_leaf, leaf_cell.p, fnk.p, fne.p, bsize.p);
-      CHECK(scan_u64(*al, bsize.p, boff.p, n_sb, tot.p, s));
+      ALLOC(sbmax, 1);
+      k_rec_size<<<blocks_for(n_slots_sb), TB, 0, s>>>(n_slots_sb, n_leaf, leaf_cell.p, fnk.p, fne.p, rsize.p);
+      PIP_CUDA(cudaMemsetAsync(rsize.p + n_slots_sb, 0, sizeof(uint64_t), s));
+      CHECK(scan_u64(*al, rsize.p, roff.p, n_slots_sb + 1, tot.p, s));
       uint64_t total16 = 0;
       CHECK(d2h(&total16, tot.p, 1, s));
       if ((uint64_t)blob_total16 + total16 >= (1ull << 32))
@@ -1350,16 +1343,19 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
       blob_lv.emplace_back();
       sbd_lv.emplace_back();
       ALLOC(blob_lv.back(), total16);
-      ALLOC(sbd_lv.back(), n_sb);
-      k_blob_fill<<<blocks_for(n_sb * 32), TB, 0, s>>>(n_sb, n_leaf, leaf_cell.p, kc_off.p, kc_poly.p,
-                                                       kc_base.p, kc_cnt.p, kc_eoff.p, kedges.p, boff.p,
-                                                       bsize.p, blob_lv.back().p, sbd_lv.back().p,
-                                                       (uint64_t)blob_total16);
+      ALLOC(sbd_lv.back(), n_slots_sb);
+      k_rec_fill<<<blocks_for(n_slots_sb * 32), TB, 0, s>>>(n_slots_sb, n_leaf, leaf_cell.p, kc_off.p, kc_poly.p,
+                                                           kc_base.p, kc_cnt.p, kc_eoff.p, kedges.p, roff.p,
+                                                           blob_lv.back().p, sbd_lv.back().p,
+                                                           (uint64_t)blob_total16);
       PIP_CUDA(cudaGetLastError());
-      // stats: largest blob
-      std::vector<uint64_t> hs(n_sb);
-      CHECK(d2h(hs.data(), bsize.p, n_sb, s));
-      for (uint64_t v : hs) max_blob16 = std::max<int64_t>(max_blob16, (int64_t)v);
+      // stats: largest superbin
+      PIP_CUDA(cudaMemsetAsync(sbmax.p, 0, sizeof(unsigned long long), s));
+      k_superbin_max<<<blocks_for(n_sb), TB, 0, s>>>(n_sb, roff.p, sbmax.p);
+      PIP_CUDA(cudaGetLastError());
+      unsigned long long hmax = 0;
+      CHECK(d2h(&hmax, sbmax.p, 1, s));
+      max_blob16 = std::max<int64_t>(max_blob16, (int64_t)hmax);
       if (o.approx_units > 0) {
         cen_lv.emplace_back();
         ALLOC(cen_lv.back(), n_sb * SB_SLOTS);
@@ -1441,7 +1437,7 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
   S->table.release();
   S->nodes.release();
   S->blobs.release();
-  S->sbdesc.release();
+  S->slot_off.release();
   S->table = std::move(desc_lv[0]);
   int64_t n_nodes = 0;
   for (int64_t l : node_len) n_nodes += l;
@@ -1457,17 +1453,21 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
   table_total = top_cells + 8 * n_nodes;
   // blobs padded by one 16-byte unit so bulk copies never read past the end
   if (!S->blobs.alloc(al, (size_t)blob_total16 + 1, s)) return fail(PIP_ENOMEM, "index: blobs");
-  if (!S->sbdesc.alloc(al, (size_t)sb_total + 1, s)) return fail(PIP_ENOMEM, "index: sbdesc");
+  // record offsets of every slot, plus one past the last record
+  if (!S->slot_off.alloc(al, (size_t)sb_total * SB_SLOTS + 1, s)) return fail(PIP_ENOMEM, "index: slot offsets");
   {
-    int64_t at16 = 0, at_sb = 0;
+    int64_t at16 = 0, at_slot = 0;
     for (size_t i = 0; i < blob_lv.size(); ++i) {
       PIP_CUDA(cudaMemcpyAsync(S->blobs.p + at16, blob_lv[i].p, blob_len[i] * sizeof(uint4),
                                cudaMemcpyDeviceToDevice, s));
-      PIP_CUDA(cudaMemcpyAsync(S->sbdesc.p + at_sb, sbd_lv[i].p, sb_len[i] * sizeof(uint2),
+      PIP_CUDA(cudaMemcpyAsync(S->slot_off.p + at_slot, sbd_lv[i].p, sb_len[i] * SB_SLOTS * sizeof(uint32_t),
                                cudaMemcpyDeviceToDevice, s));
       at16 += blob_len[i];
-      at_sb += sb_len[i];
+      at_slot += sb_len[i] * SB_SLOTS;
     }
+    const uint32_t end16 = (uint32_t)blob_total16;
+    PIP_CUDA(cudaMemcpyAsync(S->slot_off.p + at_slot, &end16, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    PIP_CUDA(cudaStreamSynchronize(s));
   }
   S->approx.release();
   if (o.approx_units > 0 && sb_total > 0) {  // approximate mode: answer of every leaf slot
@@ -1481,7 +1481,7 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
       at += sb_len[i] * SB_SLOTS;
     }
     if (!S->approx.alloc(al, (size_t)n_slots, s)) return fail(PIP_ENOMEM, "index: approximate answers");
-    k_leaf_answer<<<blocks_for(n_slots), TB, 0, s>>>(n_slots, cen.p, S->blobs.p, S->sbdesc.p, S->approx.p);
+    k_leaf_answer<<<blocks_for(n_slots), TB, 0, s>>>(n_slots, cen.p, S->blobs.p, S->slot_off.p, S->approx.p);
     PIP_CUDA(cudaGetLastError());
   }
   uint32_t e2 = 0;
@@ -1506,7 +1506,7 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
   v.table = S->table.p;
   v.nodes = S->nodes.p;
   v.blobs = S->blobs.p;
-  v.sbdesc = S->sbdesc.p;
+  v.slot_off = S->slot_off.p;
   v.approx_id = S->approx.p;  // nullptr unless approximate
   v.compact = hc[3] > 0 ? 1u : 0u;
   {  // L2-resident part of the trie: the top grid plus the first nodes (the
@@ -1534,7 +1534,7 @@ pip_status build_index(pip_set_s* S, cudaStream_t s) {
   I.superbins = sb_total;
   I.leaf_cands = leaf_cands;
   I.leaf_edges = leaf_edges;
-  I.index_bytes = top_cells * 4 + n_nodes * 32 + blob_total16 * 16 + sb_total * 8;
+  I.index_bytes = top_cells * 4 + n_nodes * 32 + blob_total16 * 16 + (sb_total * SB_SLOTS + 1) * 4;
   I.max_blob_bytes = max_blob16 * 16;
   I.compact_leaves = (int64_t)hc[3];
   I.compact_bytes = (int64_t)hc[4] * 32;

@@ -15,7 +15,7 @@
 //                 one polygon call, Sec. III-A / III).
 //   K3 cross      persistent CTAs take chunks of pts_per_cta binned points
 //                 from an atomic counter. A chunk covers a contiguous range
-//                 of superbins whose records (candidates + clipped edges) are
+//                 of leaf slots whose records (candidates + clipped edges) are
 //                 contiguous in HBM; when they fit, one cp.async.bulk copy
 //                 completed on an mbarrier stages them in shared memory
 //                 (double-buffered: the next chunk's copy flies while the
@@ -415,31 +415,30 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
   }
 }
 
-struct BlobView {
-  const uint32_t* words;  // header, candidates, edge starts
+// One leaf slot's record (layout in pip_internal.cuh).
+struct LeafRec {
+  const uint32_t* w;  // nc, cand[nc], edge_end[nc]
   const int4* edges;
 };
 
-__device__ __forceinline__ BlobView blob_view(const void* base) {
-  BlobView b;
-  b.words = (const uint32_t*)base;
-  const uint32_t nc = b.words[SB_SLOTS];
-  b.edges = (const int4*)base + ((BLOB_HEADER_WORDS + nc + nc + 1 + 3) >> 2);
-  return b;
+__device__ __forceinline__ LeafRec leaf_rec(const uint4* base) {
+  LeafRec r;
+  r.w = (const uint32_t*)base;
+  r.edges = (const int4*)(base + ((1u + 2u * r.w[0] + 3u) >> 2));
+  return r;
 }
 
 // Crossing test of one point against its leaf's candidates, in id order.
-__device__ __forceinline__ int32_t test_point(const BlobView& b, uint32_t local, int32_t qx,
-                                              int32_t qy) {
-  const uint32_t nc = b.words[SB_SLOTS];
-  const uint32_t* cand = b.words + BLOB_HEADER_WORDS;
-  const uint32_t* estart = cand + nc;
-  const uint32_t c0 = b.words[local], c1 = b.words[local + 1];
-  for (uint32_t c = c0; c < c1; ++c) {
+__device__ __forceinline__ int32_t test_point(const LeafRec& b, int32_t qx, int32_t qy) {
+  const uint32_t nc = b.w[0];
+  const uint32_t* cand = b.w + 1;
+  const uint32_t* eend = cand + nc;
+  uint32_t e = 0;
+  for (uint32_t c = 0; c < nc; ++c) {
     const uint32_t cw = cand[c];
     uint32_t par = cw >> 31;
-    const uint32_t e1 = estart[c + 1];
-    for (uint32_t e = estart[c]; e < e1; ++e) par ^= edge_crosses(b.edges[e], qx, qy);
+    const uint32_t e1 = eend[c];
+    for (; e < e1; ++e) par ^= edge_crosses(b.edges[e], qx, qy);
     if (par) return (int32_t)(cw & 0x7FFFFFFFu);
   }
   return -1;
@@ -448,36 +447,36 @@ __device__ __forceinline__ int32_t test_point(const BlobView& b, uint32_t local,
 // The same test done by the whole warp for one point (broadcast values):
 // lanes take edges lane, lane+32, ...; the parity is the popcount of the
 // ballot of the lanes' partial parities.
-__device__ __forceinline__ int32_t test_point_warp(const BlobView& b, uint32_t local, int32_t qx,
-                                                   int32_t qy) {
+__device__ __forceinline__ int32_t test_point_warp(const LeafRec& b, int32_t qx, int32_t qy) {
   const int lane = threadIdx.x & 31;
-  const uint32_t nc = b.words[SB_SLOTS];
-  const uint32_t* cand = b.words + BLOB_HEADER_WORDS;
-  const uint32_t* estart = cand + nc;
-  const uint32_t c0 = b.words[local], c1 = b.words[local + 1];
-  for (uint32_t c = c0; c < c1; ++c) {
+  const uint32_t nc = b.w[0];
+  const uint32_t* cand = b.w + 1;
+  const uint32_t* eend = cand + nc;
+  uint32_t e0 = 0;
+  for (uint32_t c = 0; c < nc; ++c) {
     const uint32_t cw = cand[c];
     uint32_t part = 0;
-    const uint32_t e1 = estart[c + 1];
-    for (uint32_t e = estart[c] + lane; e < e1; e += 32) part ^= edge_crosses(b.edges[e], qx, qy);
+    const uint32_t e1 = eend[c];
+    for (uint32_t e = e0 + lane; e < e1; e += 32) part ^= edge_crosses(b.edges[e], qx, qy);
+    e0 = e1;
     const uint32_t par = (cw >> 31) ^ (__popc(__ballot_sync(0xffffffffu, part)) & 1u);
     if (par) return (int32_t)(cw & 0x7FFFFFFFu);
   }
   return -1;
 }
 
-__device__ __forceinline__ uint32_t leaf_edges(const BlobView& b, uint32_t local) {
-  const uint32_t nc = b.words[SB_SLOTS];
-  const uint32_t* estart = b.words + BLOB_HEADER_WORDS + nc;
-  return estart[b.words[local + 1]] - estart[b.words[local]];
+__device__ __forceinline__ uint32_t leaf_edges(const LeafRec& b) {
+  const uint32_t nc = b.w[0];
+  return nc ? b.w[nc + nc] : 0u;
 }
 
 // Crossing tests of the binned residual points [first, first + count),
-// count <= 32, one per lane of the calling warp. Each point's superbin record
-// lives either in the staged copy of the chunk's contiguous record range
-// (staged != nullptr, starting at 16-byte unit region16 of the blobs) or in
-// global memory. Points whose leaf holds a long edge list are tested by the
-// whole warp. Ids go through `store`.
+// count <= 32, one per lane of the calling warp. Each point's leaf record
+// (two dependent reads: the slot's offset, then the record with candidates
+// and edges together) lives either in the staged copy of the chunk's
+// contiguous record range (staged != nullptr, starting at 16-byte unit
+// region16 of the blobs) or in global memory. Points whose leaf holds a long
+// edge list are tested by the whole warp. Ids go through `store`.
 template <class Store>
 __device__ __forceinline__ void test_warp_slice(const IndexView& ix, const Residual* __restrict__ binned,
                                                 uint32_t first, uint32_t count, const uint4* staged,
@@ -488,24 +487,22 @@ __device__ __forceinline__ void test_warp_slice(const IndexView& ix, const Resid
   const uint4* bp = ix.blobs;
   if (active) {
     r = binned[first + lane];
-    const uint2 sd = ix.sbdesc[r.w >> SB_LOG2];
-    bp = staged ? staged + (sd.x - region16) : ix.blobs + sd.x;
+    const uint32_t off = ix.slot_off[r.w];
+    bp = staged ? staged + (off - region16) : ix.blobs + off;
   }
-  BlobView b{nullptr, nullptr};
-  if (active) b = blob_view(bp);
-  const uint32_t local = r.w & (SB_SLOTS - 1);
-  const bool is_long = active && leaf_edges(b, local) > (uint32_t)LONG_LIST;
+  LeafRec b{nullptr, nullptr};
+  if (active) b = leaf_rec(bp);
+  const bool is_long = active && leaf_edges(b) > (uint32_t)LONG_LIST;
   int32_t id = -1;
-  if (active && !is_long) id = test_point(b, local, (int32_t)r.x, (int32_t)r.y);
+  if (active && !is_long) id = test_point(b, (int32_t)r.x, (int32_t)r.y);
   uint32_t lm = __ballot_sync(0xffffffffu, is_long);
   while (lm) {
     const int j = __ffs(lm) - 1;
     lm &= lm - 1;
     const int32_t px = (int32_t)__shfl_sync(0xffffffffu, r.x, j);
     const int32_t py = (int32_t)__shfl_sync(0xffffffffu, r.y, j);
-    const uint32_t lj = __shfl_sync(0xffffffffu, local, j);
     const unsigned long long pj = __shfl_sync(0xffffffffu, (unsigned long long)(uintptr_t)bp, j);
-    const int32_t v = test_point_warp(blob_view((const uint4*)(uintptr_t)pj), lj, px, py);
+    const int32_t v = test_point_warp(leaf_rec((const uint4*)(uintptr_t)pj), px, py);
     if (lane == j) id = v;
   }
   if (active) store(r, id);

@@ -12,16 +12,20 @@
 //          boundary leaves / split again, numbered from leaf_base /
 //          child_base in child order), and for the other children a 2-bit
 //          code into a 4-entry palette of polygon ids (-1 = empty).
-//   blobs  one 16-byte-aligned record per superbin (32 consecutive leaf
-//          slots), copied to shared memory by one bulk copy:
-//            u32 leaf_start[33]     candidate range of each slot
+//   blobs  one 16-byte-aligned record per leaf slot, in slot order (so
+//          the records of consecutive slots, e.g. a chunk of binned points,
+//          are one contiguous range that one bulk copy can stage):
+//            u32 nc                 kept candidates
 //            u32 cand[nc]           polygon id | base_parity << 31
-//            u32 edge_start[nc + 1] edge range of each candidate
+//            u32 edge_end[nc]       end of each candidate's edges (cumulative)
 //            (pad to 16 bytes)
 //            int4 edge[ne]          (ax, ay, bx, by) with ay <= by; an edge
 //                                   with ay == by is horizontal and never
 //                                   counts (kept only to mark the boundary)
-//   sbdesc uint2 per superbin: blob offset and size in 16-byte units.
+//          Padding slots (past a level's leaves) hold an empty record.
+//   slot_off u32 per leaf slot (+ one past the last): the record's offset
+//          in 16-byte units. Slots are grouped by 32 into superbins, the
+//          binning key of the residual points.
 //
 // Compact leaves. A boundary cell whose kept candidates (at most 3) share at
 // most a few distinct non-horizontal edges is answered in the classify
@@ -59,7 +63,6 @@ constexpr uint32_t TAG_CHILD = 3u;
 constexpr uint32_t PAYLOAD_MASK = 0x3FFFFFFFu;
 constexpr int SB_LOG2 = 5;  // 32 leaf slots per superbin
 constexpr int SB_SLOTS = 1 << SB_LOG2;
-constexpr int BLOB_HEADER_WORDS = SB_SLOTS + 1;
 constexpr int MAX_LEVELS = 12;
 constexpr uint32_t DESC_COMPACT = 1u << 29;
 constexpr int DESC_SLOTS_SHIFT = 27;
@@ -102,7 +105,7 @@ struct IndexView {
   const uint32_t* table;  // top-grid descriptors
   const uint4* nodes;     // trie nodes, two uint4 per node
   const uint4* blobs;     // superbin records (16-byte units)
-  const uint2* sbdesc;    // per superbin: (offset, size) in 16-byte units
+  const uint32_t* slot_off;  // per leaf slot (+1): record offset in 16-byte units
   const int32_t* approx_id;  // approximate mode: id per leaf slot (nullptr when exact)
 };
 
@@ -409,7 +412,7 @@ struct pip_set_s {
   pip::DBuf<uint32_t> table;
   pip::DBuf<uint4> nodes;
   pip::DBuf<uint4> blobs;
-  pip::DBuf<uint2> sbdesc;
+  pip::DBuf<uint32_t> slot_off;
   pip::DBuf<int32_t> approx;  // approximate mode: id per leaf slot
   pip::IndexView view{};
   pip_set_info_t info{};

@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(K3_THREADS) k_cross(IndexView ix, const Residu
   }
 
   // thread 0: claim the next chunk into stage st and start its copy when the
-  // chunk's superbin records fit the stage
+  // records of the chunk's superbins (one contiguous range) fit the stage
   auto claim = [&](int st) {
     const uint32_t w = atomicAdd(item_ctr, 1u);
     s_item[st] = w;
@@ -220,14 +220,16 @@ __global__ void __launch_bounds__(K3_THREADS) k_cross(IndexView ix, const Residu
     if (w < n_items) {
       const uint32_t first = w * ppc;
       const uint32_t last = min(first + ppc, n_res) - 1;
-      const uint2 da = ix.sbdesc[binned[first].w >> SB_LOG2];
-      const uint2 db = ix.sbdesc[binned[last].w >> SB_LOG2];
-      const uint32_t len16 = db.x + db.y - da.x;
+      // binned points are sorted by superbin (not by slot within one): stage
+      // whole superbins, from the first point's to the last point's
+      const uint32_t da = ix.slot_off[(binned[first].w >> SB_LOG2) << SB_LOG2];
+      const uint32_t db = ix.slot_off[((binned[last].w >> SB_LOG2) + 1) << SB_LOG2];
+      const uint32_t len16 = db - da;
       if (len16 <= stage16) {
         fence_proxy_async();
-        bulk_load(stage_mem + (size_t)st * stage16, ix.blobs + da.x, len16 * 16u, &bar[st]);
+        bulk_load(stage_mem + (size_t)st * stage16, ix.blobs + da, len16 * 16u, &bar[st]);
         s_staged[st] = 1;
-        s_region[st] = da.x;
+        s_region[st] = da;
         pending[st] = true;
       }
     }
