@@ -83,7 +83,9 @@ typedef struct {
                            in one 32-byte trie node */
   int32_t leaf_edges;   /* split a boundary cell holding more kept edges than this (0 = auto) */
   int32_t size_ratio;   /* split while cell side * ratio > smallest candidate box side
-                           (0 = auto, negative = off) */
+                           (0 = auto: 128, or 48 with compact leaves or the approximate mode;
+                           when the trie or leaves outgrow their 27 / 30-bit indices at that
+                           ratio, the build falls back to 48, then 16; negative = off) */
   int32_t pts_per_cta;  /* residual points per crossing work item (0 = auto) */
   int32_t stage_depth;  /* shared-memory stages in the crossing kernel: 1 or 2, or
                            negative for none (records read through L1/L2); 0 = auto */
@@ -282,9 +284,10 @@ pip_status pip_plan_tune(pip_plan plan, const pip_query* q, int32_t n_q, void* s
 pip_status pip_project_batch(const pip_query* q, int32_t n_q, void* stream);
 
 /* Autotuner: time candidate index shapes (cell_log2 - 1 .. + 1, split ratio
- * 16 / 32 / 48 / 64, 4 or 8 kept edges per leaf) and then crossing work items
- * (pts_per_cta 128 .. 1024, stage_depth none / 1 / 2) on a sample of the
- * set's queries (device pointers), and rebuild the set with the fastest; the
+ * 16 / 32 / 64 / 128, 4 or 8 kept edges per leaf), then compact leaves (3
+ * edges) on the fastest shape, then crossing work items (pts_per_cta
+ * 128 .. 1024, stage_depth none / 1 / 2), each on a sample of the set's
+ * queries (device pointers), and rebuild the set with the fastest; the
  * chosen options are written to *chosen (may be NULL). Synchronous. Shapes
  * whose index fails to build (too large) are skipped. */
 pip_status pip_set_tune(pip_set set, const double* lon, const double* lat, int64_t n_sample,

@@ -949,7 +949,14 @@ static void resolve_opts(const pip_build_opts& in, int64_t n_poly, long long w, 
   }
   o.max_depth = std::min(o.max_depth, std::max(0, (o.cell_log2 - (o.approx_units > 0 ? 0 : 1)) / o.fanout_log2));
   if (o.leaf_edges <= 0) o.leaf_edges = 8;
-  if (o.size_ratio == 0) o.size_ratio = 48;  // measured: deeper tries pay once K1 walks levels in bulk
+  // measured on the state workload: a deeper trie costs K1 little (it walks
+  // levels in bulk) and saves more in the residual kernels (128: 1.63 ms a
+  // step against 1.74 at 48 and 1.69 at 64). With compact leaves every leaf
+  // becomes a record in the node array, and ratio 128 overflows its 2^27
+  // slots on the state set; the approximate mode splits leaves further by
+  // its own bound. In both the automatic ratio stays 48.
+  const bool compact_asked = o.compact_edges > 0 && o.approx_units <= 0;
+  if (o.size_ratio == 0) o.size_ratio = (compact_asked || o.approx_units > 0) ? 48 : 128;
   if (o.pts_per_cta <= 0) o.pts_per_cta = 256;
   if (o.stage_depth == 0) o.stage_depth = -1;  // measured best when chunks span many superbins
   if (o.stage_depth < 0) o.stage_depth = -1;  // no shared-memory staging
@@ -1073,7 +1080,24 @@ pip_status build_grid(pip_set_s* S, Grid& g, pip_build_opts& o, Alloc* al, cudaS
   return PIP_OK;
 }
 
+static pip_status build_index_shape(pip_set_s* S, cudaStream_t s);
+
+// Build the set's index. With the split ratio left automatic, a ratio whose
+// trie or leaves outgrow their 27 / 30-bit indices (a large set with coarse
+// top cells, e.g. 800,000 blocks at ratio 128) falls back to 48, then 16.
 pip_status build_index(pip_set_s* S, cudaStream_t s) {
+  if (S->opts.size_ratio != 0) return build_index_shape(S, s);
+  pip_status st = PIP_OK;
+  for (int fallback : {0, 48, 16}) {
+    S->opts.size_ratio = fallback;
+    st = build_index_shape(S, s);
+    if (st != PIP_ERANGE) break;
+  }
+  if (st != PIP_OK) S->opts.size_ratio = 0;  // leave the caller's automatic choice in place
+  return st;
+}
+
+static pip_status build_index_shape(pip_set_s* S, cudaStream_t s) {
   Alloc* al = &S->alloc;
   cudaEvent_t ev0, ev1;
   PIP_CUDA(cudaEventCreate(&ev0));

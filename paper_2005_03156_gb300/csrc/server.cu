@@ -10,13 +10,18 @@
 // pinned memory and sent in one copy, large ones copied directly), runs the
 // plan and copies the ids back. Requests that arrive while launches are in
 // flight wait only for the next free slot, so their work overlaps the
-// running launches (continuous batching). A host callback on the stream
-// marks the requests done and records their latency. A request larger than
+// running launches (continuous batching). Each launch ends with an event on
+// its slot's stream; the dispatcher polls the events of busy slots (it
+// spins, yielding, while launches are in flight and for a short window
+// after the last activity, then sleeps until a submit wakes it), marks the
+// requests done and records their latency, so a small request's completion
+// takes no host callback and no extra thread hand-off. A request larger than
 // one launch holds is queued as consecutive parts of at most a launch each
 // (its point vector cut into ranges, Appendix A takes vectors of any
 // length); its ticket completes, and its latency is recorded, when the last
 // part is done.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -34,6 +39,8 @@ namespace {
 using Clock = std::chrono::steady_clock;
 constexpr int64_t GATHER_MAX = 1 << 15;  // requests up to this size are gathered on the CPU
 constexpr int64_t LAT_WINDOW = 1 << 22;  // latency samples kept for the percentiles
+constexpr double SPIN_IDLE_US = 200.0;   // the dispatcher keeps polling this long after activity
+constexpr double SPIN_WAIT_US = 300.0;   // pip_server_wait polls this long before it sleeps
 
 struct Req {
   uint64_t ticket = 0;
@@ -43,7 +50,7 @@ struct Req {
   int64_t n = 0;
   int32_t* out = nullptr;
   Clock::time_point t_sub, t_done;
-  int state = 0;  // 0 queued, 1 running, 2 done
+  std::atomic<int> state{0};  // 0 queued, 1 running, 2 done (written under the server's lock)
   pip_status err = PIP_OK;
   int64_t off = 0;       // offset in the slot's staging buffers
   bool gathered = false;
@@ -105,7 +112,9 @@ struct Slot {
   int32_t* hout = nullptr;
   std::vector<Req*> batch;
   bool busy = false;
+  cudaEvent_t done_ev = nullptr;  // recorded after the launch's copies back
   ~Slot() {
+    if (done_ev) cudaEventDestroy(done_ev);
     if (plan) pip_plan_destroy(plan);
     if (hlon) cudaFreeHost(hlon);
     if (hlat) cudaFreeHost(hlat);
@@ -117,16 +126,15 @@ struct Slot {
   }
 };
 
-// Host callback: the slot's launch and copies are complete.
-void CUDART_CB slot_done(void* arg) {
-  Slot* sl = (Slot*)arg;
-  pip_server_s* S = sl->srv;
+// The slot's launch and copies are complete (server lock held): hand the
+// gathered ids back, mark the requests done and record their latency.
+void complete_slot(pip_server_s* S, Slot* sl, pip_status err) {
   const auto now = Clock::now();
-  std::lock_guard<std::mutex> lk(S->mu);
   for (Req* part : sl->batch) {
-    if (part->gathered && part->n > 0) std::memcpy(part->out, sl->hout + part->off, part->n * sizeof(int32_t));
-    Req* r = finish_req(part, now, PIP_OK);
-    if (!r) continue;
+    if (err == PIP_OK && part->gathered && part->n > 0)
+      std::memcpy(part->out, sl->hout + part->off, part->n * sizeof(int32_t));
+    Req* r = finish_req(part, now, err);
+    if (!r || err != PIP_OK) continue;
     const double us = std::chrono::duration<double, std::micro>(r->t_done - r->t_sub).count();
     if ((int64_t)S->lat_us.size() < LAT_WINDOW) S->lat_us.push_back(us);
     else S->lat_us[S->lat_seen % LAT_WINDOW] = us;
@@ -180,15 +188,32 @@ pip_status launch_batch(pip_server_s* S, Slot* sl) {
     if (r->gathered || r->n == 0) continue;
     PIP_CUDA(cudaMemcpyAsync(r->out, sl->dout.p + r->off, r->n * sizeof(int32_t), cudaMemcpyDefault, s));
   }
-  PIP_CUDA(cudaLaunchHostFunc(s, slot_done, sl));
+  PIP_CUDA(cudaEventRecord(sl->done_ev, s));
   return PIP_OK;
 }
 
 void dispatch_loop(pip_server_s* S) {
   cudaSetDevice(S->device);
   std::unique_lock<std::mutex> lk(S->mu);
+  auto active = Clock::now();
   while (true) {
-    if (S->stop && S->pending.empty()) break;
+    // completions of busy slots
+    bool any_busy = false;
+    for (auto& sl : S->slots) {
+      if (!sl->busy) continue;
+      const cudaError_t q = cudaEventQuery(sl->done_ev);
+      if (q == cudaSuccess) {
+        complete_slot(S, sl.get(), PIP_OK);
+        active = Clock::now();
+      } else if (q == cudaErrorNotReady) {
+        cudaGetLastError();  // not an error: clear it from this thread's state
+        any_busy = true;
+      } else {
+        cudaGetLastError();
+        complete_slot(S, sl.get(), PIP_ECUDA);
+      }
+    }
+    if (S->stop && S->pending.empty() && !any_busy) break;
     Slot* free_slot = nullptr;
     for (auto& sl : S->slots)
       if (!sl->busy) {
@@ -196,7 +221,15 @@ void dispatch_loop(pip_server_s* S) {
         break;
       }
     if (S->pending.empty() || !free_slot) {
-      S->cv.wait(lk);
+      const double idle_us = std::chrono::duration<double, std::micro>(Clock::now() - active).count();
+      if (any_busy || idle_us < SPIN_IDLE_US) {  // keep polling, without holding the lock
+        lk.unlock();
+        std::this_thread::yield();
+        lk.lock();
+      } else {
+        S->cv.wait(lk);
+        active = Clock::now();
+      }
       continue;
     }
     // admit queued requests while the slot's capacities allow
@@ -216,11 +249,11 @@ void dispatch_loop(pip_server_s* S) {
     lk.unlock();
     pip_status st = launch_batch(S, free_slot);
     lk.lock();
+    active = Clock::now();
     if (st != PIP_OK) {  // fail the batch's requests; the slot stays usable
-      for (Req* r : free_slot->batch) finish_req(r, Clock::now(), st);
-      free_slot->batch.clear();
-      free_slot->busy = false;
-      S->cv.notify_all();
+      cudaStreamSynchronize(free_slot->s);  // nothing of the failed launch stays in flight
+      cudaGetLastError();
+      complete_slot(S, free_slot, st);
     }
   }
 }
@@ -259,6 +292,7 @@ extern "C" pip_status pip_server_create(const pip_set* sets, int32_t n_sets, con
     auto sl = std::make_unique<Slot>();
     sl->srv = S.get();
     PIP_CUDA(cudaStreamCreateWithFlags(&sl->s, cudaStreamNonBlocking));
+    PIP_CUDA(cudaEventCreateWithFlags(&sl->done_ev, cudaEventDisableTiming));
     pip_status st = pip_plan_create(S->cap_points, S->cap_queries, sl->s, &sl->plan);
     if (st != PIP_OK) return st;
     if (!sl->dlon.alloc(&sl->alloc, S->cap_points, sl->s) || !sl->dlat.alloc(&sl->alloc, S->cap_points, sl->s) ||
@@ -329,6 +363,15 @@ extern "C" pip_status pip_server_wait(pip_server srv, uint64_t ticket, int64_t t
   if (it == srv->reqs.end()) return fail(PIP_EINVAL, "pip_server_wait: unknown ticket");
   Req* r = it->second.get();
   auto done = [&] { return r->state == 2; };
+  if (!done()) {  // poll a little before sleeping: small requests finish within it
+    lk.unlock();
+    const auto t0 = Clock::now();
+    const double limit = timeout_us < 0 ? SPIN_WAIT_US : std::min<double>(SPIN_WAIT_US, (double)timeout_us);
+    while (r->state.load(std::memory_order_acquire) != 2 &&
+           std::chrono::duration<double, std::micro>(Clock::now() - t0).count() < limit)
+      std::this_thread::yield();
+    lk.lock();
+  }
   if (timeout_us < 0) {
     srv->cv.wait(lk, done);
   } else if (!srv->cv.wait_for(lk, std::chrono::microseconds(timeout_us), done)) {

@@ -58,7 +58,7 @@ extern "C" pip_status pip_set_tune(pip_set set, const double* lon, const double*
   // 1) index shape: top cell size, subdivision ratio, leaf size
   const int s0 = start.cell_log2;
   for (int dc = -1; dc <= 1; ++dc)
-    for (int ratio : {16, 32, 48, 64})
+    for (int ratio : {16, 32, 64, 128})
       for (int le : {4, 8}) {
         pip_build_opts o = start;
         o.cell_log2 = std::max(4, std::min(30, s0 + dc));
@@ -75,7 +75,22 @@ extern "C" pip_status pip_set_tune(pip_set set, const double* lon, const double*
           best = set->opts;
         }
       }
-  // 2) crossing work items on the best index
+  // 2) compact leaves on the best shape
+  {
+    pip_build_opts o = best;
+    o.compact_edges = 3;
+    set->opts = o;
+    if (build_index(set, s) == PIP_OK) {
+      float ms = 0;
+      pip_status st = time_projection(set, lon, lat, n_sample, out.p, s, 3, ms);
+      if (st != PIP_OK) return st;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = set->opts;
+      }
+    }
+  }
+  // 3) crossing work items on the best index
   set->opts = best;
   pip_status st = build_index(set, s);
   if (st != PIP_OK) return st;
