@@ -786,43 +786,41 @@ __global__ void k_superbin_max(int64_t n_sb, const uint64_t* __restrict__ off16,
     atomicMax(out, (unsigned long long)(off16[(b + 1) * SB_SLOTS] - off16[b * SB_SLOTS]));
 }
 
-// Fill the leaf records (warp per slot) and the slots' global offsets.
+// Fill the leaf records and the slots' global offsets (a thread per slot:
+// records are short; the rare long one is copied by its thread alone).
 __global__ void k_rec_fill(int64_t n_slots, int64_t n_leaf, const uint32_t* __restrict__ leaf_cell,
                            const uint64_t* __restrict__ kc_off, const int32_t* __restrict__ kc_poly,
                            const uint8_t* __restrict__ kc_base, const uint32_t* __restrict__ kc_cnt,
                            const uint64_t* __restrict__ kc_eoff, const int4* __restrict__ kedges,
                            const uint64_t* __restrict__ off16, uint4* __restrict__ blobs,
                            uint32_t* __restrict__ slot_off, uint64_t base16) {
-  const int lane = threadIdx.x & 31;
-  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t t = (((int64_t)blockIdx.x * blockDim.x) + threadIdx.x) >> 5; t < n_slots; t += warps) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n_slots;
+       t += (int64_t)gridDim.x * blockDim.x) {
     uint4* rec = blobs + off16[t];
     uint32_t* w = (uint32_t*)rec;
-    if (lane == 0) slot_off[t] = (uint32_t)(base16 + off16[t]);
+    slot_off[t] = (uint32_t)(base16 + off16[t]);
     if (t >= n_leaf) {
-      if (lane < 4) w[lane] = 0u;
+      rec[0] = make_uint4(0u, 0u, 0u, 0u);
       continue;
     }
     const uint32_t c = leaf_cell[t];
     const uint64_t k0 = kc_off[c];
     const uint32_t nc = (uint32_t)(kc_off[c + 1] - k0);
     const uint32_t head = (1u + 2u * nc + 3u) / 4u;
-    int4* edges = (int4*)(rec + head);
-    if (lane == 0) {
-      w[0] = nc;
-      uint32_t e = 0;
-      for (uint32_t i = 0; i < nc; ++i) {
-        w[1 + i] = (uint32_t)kc_poly[k0 + i] | ((uint32_t)kc_base[k0 + i] << 31);
-        e += kc_cnt[k0 + i];
-        w[1 + nc + i] = e;
-      }
-      for (uint32_t k = 1 + 2 * nc; k < 4 * head; ++k) w[k] = 0u;
+    w[0] = nc;
+    uint32_t e = 0;
+    for (uint32_t i = 0; i < nc; ++i) {
+      w[1 + i] = (uint32_t)kc_poly[k0 + i] | ((uint32_t)kc_base[k0 + i] << 31);
+      e += kc_cnt[k0 + i];
+      w[1 + nc + i] = e;
     }
+    for (uint32_t k = 1 + 2 * nc; k < 4 * head; ++k) w[k] = 0u;
+    int4* edges = (int4*)(rec + head);
     uint32_t at = 0;
     for (uint32_t i = 0; i < nc; ++i) {
       const uint32_t cnt = kc_cnt[k0 + i];
-      const uint64_t src = kc_eoff[k0 + i];
-      for (uint32_t q = lane; q < cnt; q += 32) edges[at + q] = kedges[src + q];
+      const int4* src = kedges + kc_eoff[k0 + i];
+      for (uint32_t q = 0; q < cnt; ++q) edges[at + q] = src[q];
       at += cnt;
     }
   }
@@ -1368,7 +1366,7 @@ static pip_status build_index_shape(pip_set_s* S, cudaStream_t s) {
       sbd_lv.emplace_back();
       ALLOC(blob_lv.back(), total16);
       ALLOC(sbd_lv.back(), n_slots_sb);
-      k_rec_fill<<<blocks_for(n_slots_sb * 32), TB, 0, s>>>(n_slots_sb, n_leaf, leaf_cell.p, kc_off.p, kc_poly.p,
+      k_rec_fill<<<blocks_for(n_slots_sb), TB, 0, s>>>(n_slots_sb, n_leaf, leaf_cell.p, kc_off.p, kc_poly.p,
                                                            kc_base.p, kc_cnt.p, kc_eoff.p, kedges.p, roff.p,
                                                            blob_lv.back().p, sbd_lv.back().p,
                                                            (uint64_t)blob_total16);
