@@ -134,6 +134,8 @@ typedef struct {
   int64_t compact_leaves;   /* boundary cells answered from compact records */
   int64_t compact_bytes;    /* bytes of those records (inside the trie-node array) */
   int64_t compact_by_edges[8]; /* compact leaves by number of distinct edges 0..7 */
+  int32_t size_ratio;       /* the split ratio the index was built with (after any fallback) */
+  int32_t compact_edges;    /* compact leaves' edge limit, or negative when off */
 } pip_set_info_t;
 
 /* Per-call counters of pip_project_ex (read after the stream is synchronised). */

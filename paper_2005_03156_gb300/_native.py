@@ -39,7 +39,8 @@ class SetInfo(ctypes.Structure):
                 ("max_blob_bytes", I64), ("cell_log2", I32), ("fanout_log2", I32), ("depth", I32),
                 ("cand_mode", I32), ("pts_per_cta", I32), ("stage_depth", I32), ("grid_x0", I32),
                 ("grid_y0", I32), ("grid_nx", I64), ("grid_ny", I64), ("build_ms", ctypes.c_double),
-                ("compact_leaves", I64), ("compact_bytes", I64), ("compact_by_edges", I64 * 8)]
+                ("compact_leaves", I64), ("compact_bytes", I64), ("compact_by_edges", I64 * 8),
+                ("size_ratio", I32), ("compact_edges", I32)]
 
 
 class ProjectStats(ctypes.Structure):

@@ -218,7 +218,9 @@ using namespace pip;
 
 extern "C" const char* pip_last_error(void) { return g_last_error.c_str(); }
 
-extern "C" int32_t pip_version(void) { return 10000; }
+// 1.1.0: compact leaves and the split-ratio fallback (options and set facts), pip_locate,
+// per-slot leaf records.
+extern "C" int32_t pip_version(void) { return 10100; }
 
 extern "C" int64_t pip_kernel_launches(void) { return g_launches.load(); }
 

@@ -1561,6 +1561,8 @@ static pip_status build_index_shape(pip_set_s* S, cudaStream_t s) {
   I.compact_leaves = (int64_t)hc[3];
   I.compact_bytes = (int64_t)hc[4] * 32;
   for (int e = 0; e < 8; ++e) I.compact_by_edges[e] = (int64_t)hc[5 + e];
+  I.size_ratio = o.size_ratio;
+  I.compact_edges = o.compact_edges;
   I.cell_log2 = g.s0;
   I.fanout_log2 = k;
   I.depth = depth_used;

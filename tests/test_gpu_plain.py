@@ -98,6 +98,8 @@ OPTION_CASES = [
     dict(compact_edges=2, max_depth=1),                  # compact records beside residual leaves
     dict(compact_edges=7, cell_log2=21, max_depth=8),    # coarse top grid, compact deep down
     dict(compact_edges=3, max_depth=-1, cell_log2=15),   # uniform grid of compact cells
+    dict(compact_edges=1, compact_early=1),              # compact cells stop splitting (one edge)
+    dict(compact_edges=3, compact_early=1, size_ratio=16),  # ... and up to three edges, shallow
 ]
 
 
@@ -257,6 +259,7 @@ def test_state_scale_sampled(pipm):
     and every output is a valid id."""
     ps = configs.state_set()
     s = pipm.load_polygon_set(ps)
+    assert s.info()["size_ratio"] == 128  # the automatic split ratio
     lon, lat = configs.state_points()
     dlon, dlat = dev(lon), dev(lat)
     out = pipm.pip_project(s, dlon, dlat)
