@@ -312,7 +312,12 @@ typedef struct {
   double p50_us, p99_us, max_us, mean_batch_queries;
 } pip_server_stats_t;
 
-/* Start a serving loop over resident sets (the sets must outlive it). */
+/* Start a serving loop over resident sets (the sets must outlive it). A
+ * dispatcher thread admits requests into slots and collects finished
+ * launches; while launches are in flight, and for 200 us after the last
+ * activity, it polls (yielding the CPU between polls) instead of sleeping,
+ * which keeps a small request's latency near the kernel time at the cost of
+ * one busy host thread. */
 pip_status pip_server_create(const pip_set* sets, int32_t n_sets, const pip_server_opts* opts,
                              pip_server* out);
 /* Queue a request of any size n >= 0: lon/lat/out are host memory (pinned
@@ -330,7 +335,10 @@ pip_status pip_server_create(const pip_set* sets, int32_t n_sets, const pip_serv
  * stopping server. */
 pip_status pip_server_submit(pip_server srv, int32_t set, const double* lon, const double* lat,
                              int64_t n, int32_t* out, uint64_t* ticket);
-/* Wait up to timeout_us (< 0 = forever) for a ticket. PIP_ETIMEOUT if not done. */
+/* Wait up to timeout_us (< 0 = forever) for a ticket (polling for up to
+ * 300 us before sleeping). PIP_ETIMEOUT if not done. One thread waits per
+ * ticket; once a wait reports it done (PIP_OK or the launch's error), the
+ * ticket is forgotten. */
 pip_status pip_server_wait(pip_server srv, uint64_t ticket, int64_t timeout_us);
 /* Latency percentiles of completed requests since creation or the last reset
  * (over the most recent 4,194,304 completions when there were more). */

@@ -134,7 +134,7 @@ void complete_slot(pip_server_s* S, Slot* sl, pip_status err) {
     if (err == PIP_OK && part->gathered && part->n > 0)
       std::memcpy(part->out, sl->hout + part->off, part->n * sizeof(int32_t));
     Req* r = finish_req(part, now, err);
-    if (!r || err != PIP_OK) continue;
+    if (!r || r->err != PIP_OK) continue;  // a failed request (any of its parts) is not a completion
     const double us = std::chrono::duration<double, std::micro>(r->t_done - r->t_sub).count();
     if ((int64_t)S->lat_us.size() < LAT_WINDOW) S->lat_us.push_back(us);
     else S->lat_us[S->lat_seen % LAT_WINDOW] = us;
