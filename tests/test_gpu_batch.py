@@ -142,3 +142,21 @@ def test_set_tune_keeps_results(pipm):
     got = pipm.pip_project(s, dl, da).cpu().numpy()
     assert (got == oracle.join_hier(ps, lon, lat)).all()
     assert s.info()["cell_log2"] == chosen["cell_log2"]
+
+
+def test_prepared_query_list_runs_repeatedly(pipm, sets):
+    """A query list marshalled once (Queries) and run several times gives the
+    oracle's ids each time (outputs reset between runs)."""
+    rng = np.random.default_rng(66)
+    sizes = [0, 1, 4097, 5000, 123] + list(rng.integers(1, 20000, 20))
+    qs = make_queries(sets, rng, sizes)
+    want = oracle_results(sets, qs)
+    prepared = pipm.Queries([(s, dl, da, out) for k, s, dl, da, out in qs])
+    plan = pipm.Plan(max_points=sum(sizes), max_queries=len(qs))
+    for _ in range(3):
+        for q in qs:
+            q[4].fill_(-7)
+        plan.run(prepared)
+        plan.check()
+        for i, ((k, s, dl, da, out), w) in enumerate(zip(qs, want)):
+            assert (out.cpu().numpy() == w).all(), i
