@@ -615,9 +615,8 @@ def serve_leg(pipm, psets, loads, nreq):
 
         # served: submit on schedule, collect completions
         srv = pipm.Server(sets, dict(n_streams=3, max_batch_points=1 << 23, max_batch_queries=1024))
-        for w in range(12):  # warm every slot (graph capture happens on a slot's first launch)
-            k, lon, lat, out = req(w)
-            tw = [srv.submit(k, lon, lat, out) for _ in range(3)]
+        for w in range(4):  # warm-up: 12 requests at once, so every slot runs
+            tw = [srv.submit(*req(j)) for j in range(12)]
             for t in tw:
                 srv.wait(t)
         srv.stats(reset=True)

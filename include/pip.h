@@ -317,7 +317,9 @@ typedef struct {
  * launches; while launches are in flight, and for 200 us after the last
  * activity, it polls (yielding the CPU between polls) instead of sleeping,
  * which keeps a small request's latency near the kernel time at the cost of
- * one busy host thread. */
+ * one busy host thread. Each slot's batched plan is sized for all the sets
+ * and its launch graphs are captured here, so no request waits for an
+ * allocation or a graph capture. */
 pip_status pip_server_create(const pip_set* sets, int32_t n_sets, const pip_server_opts* opts,
                              pip_server* out);
 /* Queue a request of any size n >= 0: lon/lat/out are host memory (pinned

@@ -400,6 +400,7 @@ struct pip_plan_s {
   int grid = 0;
   int staged = 0;      // 0 unstaged, 1 staged
   bool compact = false;  // the captured kernel handles compact leaves
+  bool compact_fixed = false;  // keep `compact` for runs without compact sets
   uint32_t ppc = 256;
   uint32_t stage_bytes = 16 * 1024;  // small: the one kernel's other phases want L1
   Alloc alloc;
@@ -619,6 +620,7 @@ extern "C" pip_status pip_plan_run(pip_plan plan, const pip_query* q, int32_t n_
     hs[i].sb_base = sb_base[i];
     any_compact |= sets[i]->view.compact != 0;
   }
+  if (plan->compact_fixed) any_compact |= plan->compact;
   if (any_compact != plan->compact) {  // the other kernel instantiation: capture again
     PIP_CUDA(cudaDeviceSynchronize());
     plan->drop_graphs();
@@ -695,6 +697,32 @@ extern "C" pip_status pip_plan_destroy(pip_plan plan) {
 
 // Plan knobs used by the autotuner (internal).
 namespace pip {
+// Make a plan ready for runs over a known family of sets: superbin buffers
+// for `superbins` in all (the sum over the sets a run may use), the kernel
+// instantiation for `compact` kept for every run, and both graphs captured
+// and uploaded, so no run over those sets allocates or captures.
+pip_status plan_prepare(pip_plan plan, int64_t superbins, bool compact, cudaStream_t s) {
+  pip_status st = plan_alloc_sb(plan, superbins + 1, s);
+  if (st != PIP_OK) return st;
+  if (compact != plan->compact) {
+    plan->drop_graphs();
+    plan->compact = compact;
+    st = plan_grid(plan);
+    if (st != PIP_OK) return st;
+    if (!plan->partial.alloc(&plan->alloc, (size_t)plan->grid + 1, s))
+      return fail(PIP_ENOMEM, "pip_plan: partials");
+  }
+  plan->compact_fixed = true;
+  plan_fill_bufs(plan);
+  for (int t = 0; t < 2; ++t) {
+    st = plan_capture(plan, t, s);
+    if (st != PIP_OK) return st;
+    PIP_CUDA(cudaGraphUpload(plan->exec[t], s));
+  }
+  PIP_CUDA(cudaStreamSynchronize(s));
+  return PIP_OK;
+}
+
 pip_status plan_set_knobs(pip_plan plan, uint32_t ppc, int staged) {
   if (plan->ppc == ppc && plan->staged == staged) return PIP_OK;
   plan->ppc = ppc;

@@ -34,6 +34,10 @@
 
 #include "pip_internal.cuh"
 
+namespace pip {
+pip_status plan_prepare(pip_plan plan, int64_t superbins, bool compact, cudaStream_t s);
+}
+
 namespace {
 
 using Clock = std::chrono::steady_clock;
@@ -288,12 +292,22 @@ extern "C" pip_status pip_server_create(const pip_set* sets, int32_t n_sets, con
   S->cap_points = std::min<int64_t>(o.max_batch_points, o.mem_budget_bytes / (per_point * o.n_streams));
   if (S->cap_points < 1) return fail(PIP_ENOMEM, "pip_server_create: memory budget too small");
   S->cap_queries = o.max_batch_queries;
+  int64_t superbins = 0;
+  bool compact = false;
+  for (pip_set set : S->sets) {
+    superbins += std::max<int64_t>(1, set->view.n_sb);
+    compact |= set->view.compact != 0;
+  }
   for (int i = 0; i < o.n_streams; ++i) {
     auto sl = std::make_unique<Slot>();
     sl->srv = S.get();
     PIP_CUDA(cudaStreamCreateWithFlags(&sl->s, cudaStreamNonBlocking));
     PIP_CUDA(cudaEventCreateWithFlags(&sl->done_ev, cudaEventDisableTiming));
     pip_status st = pip_plan_create(S->cap_points, S->cap_queries, sl->s, &sl->plan);
+    if (st != PIP_OK) return st;
+    // buffers for every resident set at once and both graphs captured now:
+    // no batch allocates or captures mid-service
+    st = plan_prepare(sl->plan, superbins, compact, sl->s);
     if (st != PIP_OK) return st;
     if (!sl->dlon.alloc(&sl->alloc, S->cap_points, sl->s) || !sl->dlat.alloc(&sl->alloc, S->cap_points, sl->s) ||
         !sl->dout.alloc(&sl->alloc, S->cap_points, sl->s))
