@@ -136,6 +136,7 @@ typedef struct {
   int64_t compact_by_edges[8]; /* compact leaves by number of distinct edges 0..7 */
   int32_t size_ratio;       /* the split ratio the index was built with (after any fallback) */
   int32_t compact_edges;    /* compact leaves' edge limit, or negative when off */
+  int64_t nodes_by_level[8]; /* trie nodes (32 bytes each) of levels 1..8 below the top grid */
 } pip_set_info_t;
 
 /* Per-call counters of pip_project_ex (read after the stream is synchronised). */

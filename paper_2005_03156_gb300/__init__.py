@@ -130,6 +130,7 @@ def pip_set_info(s: PolygonSet) -> dict:
     _native.check(lib().pip_set_info(s.handle, ctypes.byref(info)))
     d = {k: getattr(info, k) for k, _ in SetInfo._fields_}
     d["compact_by_edges"] = list(d["compact_by_edges"])
+    d["nodes_by_level"] = list(d["nodes_by_level"])
     return d
 
 

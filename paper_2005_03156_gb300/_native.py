@@ -40,7 +40,7 @@ class SetInfo(ctypes.Structure):
                 ("cand_mode", I32), ("pts_per_cta", I32), ("stage_depth", I32), ("grid_x0", I32),
                 ("grid_y0", I32), ("grid_nx", I64), ("grid_ny", I64), ("build_ms", ctypes.c_double),
                 ("compact_leaves", I64), ("compact_bytes", I64), ("compact_by_edges", I64 * 8),
-                ("size_ratio", I32), ("compact_edges", I32)]
+                ("size_ratio", I32), ("compact_edges", I32), ("nodes_by_level", I64 * 8)]
 
 
 class ProjectStats(ctypes.Structure):

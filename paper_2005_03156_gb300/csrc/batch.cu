@@ -251,6 +251,21 @@ __global__ void __launch_bounds__(B_THREADS, 3) k_batch(PlanBufs B) {
           z[j] = j0 + j;
           sh[j] = (int)s0 - NODE_K;
         }
+        if (!COMPACT) {  // the first trie level at once, as the plain classify kernel
+          uint4 e[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if ((d[j] >> 30) == TAG_CHILD) e[j] = ld_entry(ix.nodes, d[j] & PAYLOAD_MASK, pol);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if ((d[j] >> 30) == TAG_CHILD) {
+              const uint32_t dx = (uint32_t)qx[j] - (uint32_t)ix.gx0, dy = (uint32_t)qy[j] - (uint32_t)ix.gy0;
+              const uint32_t m = (1u << NODE_K) - 1u;
+              d[j] = entry_step(e[j], (((dy >> sh[j]) & m) << NODE_K) | ((dx >> sh[j]) & m));
+              sh[j] = sh[j] > NODE_K ? sh[j] - NODE_K : 0;
+            }
+          }
+        }
         uint32_t leaf = 0, split = 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {

@@ -546,6 +546,100 @@ __global__ void k_node_finish(int64_t n_parent, const uint32_t* __restrict__ fc_
   }
 }
 
+// ---- 16-byte entries (an index without compact leaves) -------------------
+// Codes of a 32-byte node's children in the 16-byte form. Of the polygons
+// its EMPTY / INTERIOR children name, the two that most children name take
+// codes 0 and 1 (a, b); empty children take code 2; split and leaf
+// children, and children naming any other polygon, descend (code 3) to an
+// entry of their own.
+__device__ __forceinline__ void e16_codes(const TrieNode& nd, uint32_t& codes, int32_t& a, int32_t& b) {
+  const uint32_t lm = nd.masks & 0xFFFFu, cm = nd.masks >> 16;
+  int cnt[4] = {0, 0, 0, 0};
+  for (int sub = 0; sub < NODE_FAN; ++sub)
+    if (!((lm | cm) >> sub & 1u)) ++cnt[(nd.codes >> (2 * sub)) & 3u];
+  int ia = -1, ib = -1;  // palette entries taking codes 0 and 1
+  for (int j = 0; j < 4; ++j) {
+    if (cnt[j] == 0 || nd.pal[j] < 0) continue;
+    if (ia < 0 || cnt[j] > cnt[ia]) {
+      ib = ia;
+      ia = j;
+    } else if (ib < 0 || cnt[j] > cnt[ib]) {
+      ib = j;
+    }
+  }
+  a = ia >= 0 ? nd.pal[ia] : -1;
+  b = ib >= 0 ? nd.pal[ib] : -1;
+  codes = 0;
+  for (int sub = 0; sub < NODE_FAN; ++sub) {
+    uint32_t c = E16_DESCEND;
+    if (!((lm | cm) >> sub & 1u)) {
+      const int j = (int)((nd.codes >> (2 * sub)) & 3u);
+      c = nd.pal[j] < 0 ? E16_EMPTY : j == ia ? 0u : j == ib ? 1u : E16_DESCEND;
+    }
+    codes |= c << (2 * sub);
+  }
+}
+
+__device__ __forceinline__ uint32_t e16_ndesc(uint32_t codes) {
+  return __popc(codes & (codes >> 1) & 0x55555555u);
+}
+
+__device__ __forceinline__ uint4 e16_node(const TrieNode& nd, uint64_t base) {
+  uint32_t codes;
+  int32_t a, b;
+  e16_codes(nd, codes, a, b);
+  return make_uint4(codes, (uint32_t)base | (E16_NODE << 30), (uint32_t)a, (uint32_t)b);
+}
+
+// Descending children of each node.
+__global__ void k_e16_count(int64_t n, const TrieNode* __restrict__ old, uint32_t* __restrict__ n_desc) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t codes;
+    int32_t a, b;
+    e16_codes(old[i], codes, a, b);
+    n_desc[i] = e16_ndesc(codes);
+  }
+}
+
+// Level-1 entries keep their nodes' indices (the top grid names them).
+// rel: each node's first descending child, relative to the next level.
+__global__ void k_e16_first(int64_t n1, const TrieNode* __restrict__ old, const uint64_t* __restrict__ rel,
+                            uint64_t next_start, uint4* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n1; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = e16_node(old[i], next_start + rel[i]);
+}
+
+// The entries of the descending children of nodes [lo, lo + n) (one level):
+// a split child's node, a leaf child's slot, or the polygon of a child
+// outside its parent's two codes.
+__global__ void k_e16_children(int64_t lo, int64_t n, const TrieNode* __restrict__ old,
+                               const uint64_t* __restrict__ rel, uint64_t next_start, uint64_t next2_start,
+                               uint4* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = lo + i;
+    const TrieNode nd = old[p];
+    uint32_t codes;
+    int32_t a, b;
+    e16_codes(nd, codes, a, b);
+    const uint32_t lm = nd.masks & 0xFFFFu, cm = nd.masks >> 16;
+    uint64_t e = next_start + rel[p];
+    for (int sub = 0; sub < NODE_FAN; ++sub) {
+      if (((codes >> (2 * sub)) & 3u) != E16_DESCEND) continue;
+      const uint32_t bit = 1u << sub, below = bit - 1u;
+      uint4 v;
+      if (cm & bit) {
+        const uint32_t oc = nd.child_base + __popc(cm & below);
+        v = e16_node(old[oc], next2_start + rel[oc]);
+      } else if (lm & bit) {
+        v = make_uint4(nd.leaf_base + __popc(lm & below), E16_LEAF << 30, 0u, 0u);
+      } else {
+        v = make_uint4((uint32_t)nd.pal[(nd.codes >> (2 * sub)) & 3u], E16_ID << 30, 0u, 0u);
+      }
+      out[e++] = v;
+    }
+  }
+}
+
 __global__ void k_eff_nk(int64_t n, const uint32_t* __restrict__ fc_nk, const uint32_t* __restrict__ fc_leaf,
                          const uint32_t* __restrict__ fc_split, uint32_t* __restrict__ out) {
   for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n;
@@ -893,6 +987,64 @@ pip_status d2h(T* h, const T* d, size_t n, cudaStream_t s) {
     if (!(buf).alloc(al, (size_t)(n) + 1, s))                               \
       return fail(PIP_ENOMEM, "index build: device allocation failed");     \
   } while (0)
+
+// Convert the trie's 32-byte nodes (levels concatenated: node_len[i] nodes
+// for the split cells of level i) to 16-byte entries. *done stays false,
+// and the nodes stay, when the entries would not fit their 30-bit indices.
+pip_status to_entries16(Alloc* al, DBuf<uint4>& nodes, const std::vector<int64_t>& node_len,
+                        int64_t* n_entries, bool* done, cudaStream_t s) {
+  *done = false;
+  *n_entries = 0;
+  const size_t L = node_len.size();
+  int64_t n_nodes = 0;
+  for (int64_t l : node_len) n_nodes += l;
+  DBuf<uint4> out;
+  if (n_nodes == 0) {
+    ALLOC(out, 0);
+    PIP_CUDA(cudaMemsetAsync(out.p, 0, sizeof(uint4), s));
+    nodes = std::move(out);
+    *done = true;
+    return PIP_OK;
+  }
+  const TrieNode* old = reinterpret_cast<const TrieNode*>(nodes.p);
+  DBuf<uint32_t> nd;
+  DBuf<uint64_t> rel, tot;
+  ALLOC(nd, n_nodes);
+  ALLOC(rel, n_nodes);
+  ALLOC(tot, L);
+  k_e16_count<<<blocks_for(n_nodes), TB, 0, s>>>(n_nodes, old, nd.p);
+  PIP_CUDA(cudaGetLastError());
+  int64_t lo = 0;
+  for (size_t i = 0; i < L; ++i) {  // each node's first descending child within the next level
+    CHECK(scan_u32_to_u64(*al, nd.p + lo, rel.p + lo, node_len[i], tot.p + i, s));
+    lo += node_len[i];
+  }
+  std::vector<uint64_t> desc(L);
+  CHECK(d2h(desc.data(), tot.p, L, s));
+  // entries of level i + 1 (i = 0: the level-1 nodes) start at start[i]
+  std::vector<uint64_t> start(L + 2, 0);
+  start[1] = (uint64_t)node_len[0];
+  for (size_t i = 0; i < L; ++i) start[i + 2] = start[i + 1] + desc[i];
+  const uint64_t total = start[L + 1];
+  if (total >= (1ull << 30)) return PIP_OK;
+  ALLOC(out, total);
+  k_e16_first<<<blocks_for(node_len[0]), TB, 0, s>>>(node_len[0], old, rel.p, start[1], out.p);
+  PIP_CUDA(cudaGetLastError());
+  lo = 0;
+  for (size_t i = 0; i < L; ++i) {
+    if (node_len[i] > 0) {
+      k_e16_children<<<blocks_for(node_len[i]), TB, 0, s>>>(lo, node_len[i], old, rel.p, start[i + 1],
+                                                            start[i + 2], out.p);
+      PIP_CUDA(cudaGetLastError());
+    }
+    lo += node_len[i];
+  }
+  PIP_CUDA(cudaStreamSynchronize(s));
+  nodes = std::move(out);
+  *n_entries = (int64_t)total;
+  *done = true;
+  return PIP_OK;
+}
 
 }  // namespace
 
@@ -1510,6 +1662,11 @@ static pip_status build_index_shape(pip_set_s* S, cudaStream_t s) {
   CHECK(d2h(&e2, err.p, 1, s));
   unsigned long long hc[13];
   CHECK(d2h(hc, counters, 13, s));
+  // a trie without compact leaves is walked as 16-byte entries
+  int64_t n_entries = 0;
+  bool entries16 = false;
+  if (hc[3] == 0) CHECK(to_entries16(al, S->nodes, node_len, &n_entries, &entries16, s));
+  if (entries16) table_total = top_cells + 4 * n_entries;
   PIP_CUDA(cudaEventRecord(ev1, s));
   PIP_CUDA(cudaEventSynchronize(ev1));
   float ms = 0;
@@ -1530,7 +1687,7 @@ static pip_status build_index_shape(pip_set_s* S, cudaStream_t s) {
   v.blobs = S->blobs.p;
   v.slot_off = S->slot_off.p;
   v.approx_id = S->approx.p;  // nullptr unless approximate
-  v.compact = hc[3] > 0 ? 1u : 0u;
+  v.compact = entries16 ? 0u : 1u;
   {  // L2-resident part of the trie: the top grid plus the first nodes (the
      // shallow levels come first) up to three quarters of the L2
     int dev = 0, l2 = 0;
@@ -1540,7 +1697,8 @@ static pip_status build_index_shape(pip_set_s* S, cudaStream_t s) {
       l2 = 64 << 20;
     }
     const int64_t budget = (int64_t)l2 * 3 / 4 - top_cells * 4;
-    v.hot_nodes = (uint32_t)std::max<int64_t>(0, std::min<int64_t>(n_nodes, budget / 32));
+    v.hot_nodes = (uint32_t)std::max<int64_t>(0, entries16 ? std::min<int64_t>(n_entries, budget / 16)
+                                                            : std::min<int64_t>(n_nodes, budget / 32));
   }
 
   pip_set_info_t& I = S->info;
@@ -1556,13 +1714,15 @@ static pip_status build_index_shape(pip_set_s* S, cudaStream_t s) {
   I.superbins = sb_total;
   I.leaf_cands = leaf_cands;
   I.leaf_edges = leaf_edges;
-  I.index_bytes = top_cells * 4 + n_nodes * 32 + blob_total16 * 16 + (sb_total * SB_SLOTS + 1) * 4;
+  I.index_bytes = top_cells * 4 + (entries16 ? n_entries * 16 : n_nodes * 32) + blob_total16 * 16 +
+                  (sb_total * SB_SLOTS + 1) * 4;
   I.max_blob_bytes = max_blob16 * 16;
   I.compact_leaves = (int64_t)hc[3];
   I.compact_bytes = (int64_t)hc[4] * 32;
   for (int e = 0; e < 8; ++e) I.compact_by_edges[e] = (int64_t)hc[5 + e];
   I.size_ratio = o.size_ratio;
   I.compact_edges = o.compact_edges;
+  for (size_t l = 0; l < 8; ++l) I.nodes_by_level[l] = l < node_len.size() ? node_len[l] : 0;
   I.cell_log2 = g.s0;
   I.fanout_log2 = k;
   I.depth = depth_used;

@@ -3,10 +3,12 @@
 //
 //   K1 classify   streams the points (two 16-byte loads of lon and two of lat
 //                 per 4 points), quantizes them with integer instructions and
-//                 reads their top-grid descriptors; EMPTY and INTERIOR cells
-//                 answer at once (Sec. IV true-hit filtering). Points in split
-//                 cells wait in a per-warp ring (TrieRing) that is walked one
-//                 trie level for 128 points at a time. Points in boundary
+//                 reads their top-grid descriptors (and the first trie level
+//                 when the trie is stored as 16-byte entries); EMPTY and
+//                 INTERIOR cells answer at once (Sec. IV true-hit filtering).
+//                 Points in cells split further wait in a per-warp ring
+//                 (TrieRing) that is walked one trie level for 128 points at
+//                 a time. Points in boundary
 //                 leaves go to the residual queue through per-warp chunks
 //                 (ChunkWriter) and are counted per superbin.
 //   K2 bin        counting sort of the residual by superbin: scan of the
@@ -57,6 +59,21 @@ __device__ __forceinline__ void lookup4(const IndexView& ix, const int32_t (&qx)
   }
   int s = ix.s0;
   const uint32_t m = (1u << NODE_K) - 1u;
+  if (!ix.compact) {  // 16-byte entries
+#pragma unroll 1
+    while (((d[0] >> 30) == TAG_CHILD) | ((d[1] >> 30) == TAG_CHILD) | ((d[2] >> 30) == TAG_CHILD) |
+           ((d[3] >> 30) == TAG_CHILD)) {
+      s = s > NODE_K ? s - NODE_K : 0;  // leaf and id entries sit one level below their cell
+      uint4 e[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if ((d[j] >> 30) == TAG_CHILD) e[j] = ld_entry(ix.nodes, d[j] & PAYLOAD_MASK, pol);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if ((d[j] >> 30) == TAG_CHILD) d[j] = entry_step(e[j], (((dy[j] >> s) & m) << NODE_K) | ((dx[j] >> s) & m));
+    }
+    return;
+  }
 #pragma unroll 1
   while (((d[0] >> 30) == TAG_CHILD) | ((d[1] >> 30) == TAG_CHILD) | ((d[2] >> 30) == TAG_CHILD) |
          ((d[3] >> 30) == TAG_CHILD)) {
@@ -268,11 +285,17 @@ struct TrieRing {
     count -= take;
     __syncwarp();  // every entry is read before the pushes below reuse slots
     NodeWords nw[4];
+    uint4 ne[4];
     const uint64_t cold = policy_evict_first();
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-      const uint32_t sl = d[j] & SLOT_MASK;
-      if ((have >> j) & 1u) nw[j] = ld_node(ix.nodes, sl, sl < ix.hot_nodes ? pol : cold);
+      if (COMPACT) {
+        const uint32_t sl = d[j] & SLOT_MASK;
+        if ((have >> j) & 1u) nw[j] = ld_node(ix.nodes, sl, sl < ix.hot_nodes ? pol : cold);
+      } else {
+        const uint32_t sl = d[j] & PAYLOAD_MASK;
+        if ((have >> j) & 1u) ne[j] = ld_entry(ix.nodes, sl, sl < ix.hot_nodes ? pol : cold);
+      }
     }
     uint32_t leaf = 0, again = 0;
     if (COMPACT) {  // compact leaves: answered here, one entry per pass of a
@@ -305,7 +328,8 @@ struct TrieRing {
       if ((have >> j) & 1u) {
         const uint32_t dx = (uint32_t)qx[j] - (uint32_t)ix.gx0, dy = (uint32_t)qy[j] - (uint32_t)ix.gy0;
         const uint32_t sub = (((dy >> sh[j]) & m) << NODE_K) | ((dx >> sh[j]) & m);
-        d[j] = node_step<COMPACT>(nw[j], sub);
+        if (COMPACT) d[j] = node_step<true>(nw[j], sub);
+        else d[j] = entry_step(ne[j], sub);
         const uint32_t tag = d[j] >> 30;
         if (tag == TAG_INTERIOR) out_base[z[j]] = (int32_t)(d[j] & PAYLOAD_MASK);
         if (tag == TAG_LEAF && ix.approx_id) {  // approximate mode: the leaf's own answer
@@ -314,7 +338,7 @@ struct TrieRing {
           leaf |= (tag == TAG_LEAF ? 1u : 0u) << j;
         }
         again |= (tag == TAG_CHILD ? 1u : 0u) << j;
-        sh[j] -= NODE_K;
+        sh[j] = sh[j] > NODE_K ? sh[j] - NODE_K : 0;  // 16-byte leaf / id entries sit one level below
       }
     }
     if (__any_sync(full, leaf != 0u))

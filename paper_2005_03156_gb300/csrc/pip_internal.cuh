@@ -7,11 +7,25 @@
 //            TAG_INTERIOR  payload = polygon id answering every point
 //            TAG_LEAF      payload = leaf slot: the crossing test decides
 //            TAG_CHILD     payload = index of the cell's trie node
-//   nodes  one 32-byte node (one DRAM sector) per split cell, describing its
+//   nodes  the trie, in one of two forms (IndexView::compact says which):
+//          32-byte nodes (one DRAM sector) per split cell, describing its
 //          4 x 4 children: a leaf mask and a child mask (children that are
 //          boundary leaves / split again, numbered from leaf_base /
 //          child_base in child order), and for the other children a 2-bit
-//          code into a 4-entry palette of polygon ids (-1 = empty).
+//          code into a 4-entry palette of polygon ids (-1 = empty). An
+//          index without compact leaves converts them, once built, to
+//          16-byte entries (half the bytes per node, so twice the nodes per
+//          L2 line; the walk reads one entry per level):
+//            node  w0 = 2-bit code per child: 0 -> polygon w2, 1 -> polygon
+//                  w3, 2 -> empty, 3 -> descend to entry (w1 & 2^30 - 1) +
+//                  the child's rank among the node's code-3 children;
+//                  w1 bits 30-31 = 0
+//            leaf  w0 = leaf slot (a boundary leaf child); w1 bits 30-31 = 1
+//            id    w0 = polygon id (a child whose polygon is neither w2 nor
+//                  w3 of its parent); w1 bits 30-31 = 2
+//          The top grid names a level-1 entry; the entries of each level
+//          follow the previous level's, a node's descending children
+//          contiguous in child order.
 //   blobs  one 16-byte-aligned record per leaf slot, in slot order (so
 //          the records of consecutive slots, e.g. a chunk of binned points,
 //          are one contiguous range that one bulk copy can stage):
@@ -100,8 +114,9 @@ struct IndexView {
   int32_t s0;             // log2 side of a top cell
   int32_t depth;          // deepest level present (trie levels below the top grid)
   uint32_t n_sb;          // superbins
-  uint32_t hot_nodes;     // nodes [0, hot_nodes) (the shallow levels) are kept in L2
-  uint32_t compact;       // 1: the trie holds compact leaves (see above)
+  uint32_t hot_nodes;     // nodes / entries [0, hot_nodes) (the shallow levels) are kept in L2
+  uint32_t compact;       // 1: 32-byte nodes (which may hold compact leaves);
+                          // 0: 16-byte entries
   const uint32_t* table;  // top-grid descriptors
   const uint4* nodes;     // trie nodes, two uint4 per node
   const uint4* blobs;     // superbin records (16-byte units)
@@ -186,6 +201,35 @@ __device__ __forceinline__ uint32_t node_step(const NodeWords& n, uint32_t sub) 
   const uint32_t code = (n.w[1] >> (2 * sub)) & 3u;
   const int32_t id = (int32_t)(code == 0 ? n.w[4] : code == 1 ? n.w[5] : code == 2 ? n.w[6] : n.w[7]);
   return id < 0 ? make_desc(TAG_EMPTY, 0) : make_desc(TAG_INTERIOR, (uint32_t)id);
+}
+
+// 16-byte trie entries (see the layout above).
+constexpr uint32_t E16_NODE = 0u, E16_LEAF = 1u, E16_ID = 2u;  // w1 bits 30-31
+constexpr uint32_t E16_EMPTY = 2u, E16_DESCEND = 3u;           // child codes
+constexpr uint32_t E16_BASE_MASK = (1u << 30) - 1u;
+
+__device__ __forceinline__ uint4 ld_entry(const uint4* nodes, uint32_t e, uint64_t pol) {
+  uint4 r;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+               : "l"(nodes + e), "l"(pol));
+  return r;
+}
+
+// One trie step on a 16-byte entry: child `sub` of a node entry, or the
+// answer a leaf / id entry holds (sub unused). Returns a descriptor as
+// node_step does (TAG_CHILD: payload = entry index).
+__device__ __forceinline__ uint32_t entry_step(const uint4& n, uint32_t sub) {
+  const uint32_t kind = n.y >> 30;
+  if (kind == E16_LEAF) return make_desc(TAG_LEAF, n.x);
+  if (kind == E16_ID) return make_desc(TAG_INTERIOR, n.x);
+  const uint32_t code = (n.x >> (2 * sub)) & 3u;
+  if (code == E16_DESCEND) {
+    const uint32_t desc = n.x & (n.x >> 1) & 0x55555555u;  // bit 2c: child c descends
+    return make_desc(TAG_CHILD, (n.y & E16_BASE_MASK) + __popc(desc & ((1u << (2 * sub)) - 1u)));
+  }
+  if (code == E16_EMPTY) return make_desc(TAG_EMPTY, 0);
+  return make_desc(TAG_INTERIOR, code ? n.w : n.z);
 }
 
 // Residual entry: a point that fell in a boundary leaf.

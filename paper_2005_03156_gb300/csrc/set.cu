@@ -268,6 +268,12 @@ __global__ void k_locate(IndexView ix, const int32_t* __restrict__ qx, const int
     uint32_t d = ix.table[(size_t)cy * ix.nx + cx];
     uint32_t depth = 0;
     int s = ix.s0;
+    while (!ix.compact && (d >> 30) == TAG_CHILD) {  // 16-byte entries
+      s = s > NODE_K ? s - NODE_K : 0;
+      const uint4 e = ix.nodes[d & PAYLOAD_MASK];
+      if ((e.y >> 30) == E16_NODE) ++depth;  // leaf and id entries belong to their parent's level
+      d = entry_step(e, (((dy >> s) & m) << NODE_K) | ((dx >> s) & m));
+    }
     while ((d >> 30) == TAG_CHILD && !(d & DESC_COMPACT)) {
       s -= NODE_K;
       const uint32_t* w = reinterpret_cast<const uint32_t*>(ix.nodes + 2 * (size_t)(d & SLOT_MASK));
