@@ -7,8 +7,8 @@ counts, 2% holes) over 5x5 degrees and 1e8 float64 mixture points.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--config state|tiny] [--points N] [--no-e2e] [--no-cpu-baseline]
 
-One step = one pip_project call over the whole batch (K1 classify + K2 bin +
-K3 cross), inputs resident in HBM. Under torchrun (N > 1) every rank
+One step = one pip_project call over the whole batch (K1 classify, K2 bin
+when binning is on, K3 cross), inputs resident in HBM. Under torchrun (N > 1) every rank
 projects its own 1e8 points against a replica of the set (weak scaling, no
 collective on the data path); value = all ranks' points / max rank time.
 At N = 1 the same line also carries the metric's two other parts, measured
@@ -413,7 +413,7 @@ def run_ours(args):
                          "bytes_per_launch": BYTES_PER_POINT * n,
                          "step": {"achieved": BYTES_PER_POINT * n / (ms_step / 1e3) / 1e9,
                                   "frac": BYTES_PER_POINT * n / (ms_step / 1e3) / 1e9 / peak,
-                                  "note": "the whole projection (K1 + K2 + K3) against the same 20 B/point"}},
+                                  "note": "the whole projection (K1, K3 and, when binning is on, K2) against the same 20 B/point"}},
             "stages_ms": {"k1_classify": k1, "k2_bin": bn, "k3_cross": k3},
             "e2e": e2e, "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
         }

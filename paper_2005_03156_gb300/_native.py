@@ -28,7 +28,7 @@ class BuildOpts(ctypes.Structure):
     _fields_ = [("cell_log2", I32), ("max_depth", I32), ("fanout_log2", I32), ("leaf_edges", I32),
                 ("size_ratio", I32), ("pts_per_cta", I32), ("stage_depth", I32), ("cand_mode", I32),
                 ("approx_units", I32), ("compact_edges", I32),
-                ("compact_early", I32)]
+                ("compact_early", I32), ("bin_residual", I32)]
 
 
 class SetInfo(ctypes.Structure):

@@ -15,6 +15,9 @@
 //                is staged with one cp.async.bulk copy; then the exact
 //                crossing test runs per point and the id is written to its
 //                query's output.
+// Phases 1 and 2 run only with staging, which needs a chunk's records
+// contiguous; unstaged (the default), phase 3 reads the residual queue in
+// arrival order, as the plain path does: binning cost more than it saved.
 // The results equal separate plain projections bit for bit: same index,
 // same arithmetic, same rule.
 #include <algorithm>
@@ -122,11 +125,12 @@ __device__ __forceinline__ void batch_test_chunk(const DevSet* sets, uint32_t n_
   const int lane = threadIdx.x & 31;
   for (uint32_t base = threadIdx.x & ~31u; base < count; base += blockDim.x) {
     const uint32_t t = base + lane;
-    const bool active = t < count;
+    bool active = t < count;
     Residual r = make_uint4(0, 0, 0, 0);
     const uint4* bp = nullptr;
+    if (active) r = binned[first + t];
+    active &= r.w != RES_HOLE;  // the queue in arrival order keeps its unused entries
     if (active) {
-      r = binned[first + t];
       const DevSet& S = sets[set_of_slot(sets, n_sets, r.w)];
       const uint32_t off = S.view.slot_off[r.w - (S.sb_base << SB_LOG2)];
       bp = staged ? staged + (off - region16) : S.view.blobs + off;
@@ -298,68 +302,73 @@ __global__ void __launch_bounds__(B_THREADS, 3) k_batch(PlanBufs B) {
   }
   grid_barrier(B, nblocks);
 
-  // ---- phase 1: exclusive scan of hist[0, n_sb_total) over all CTAs
-  const uint32_t nsb = H.n_sb_total;
-  const uint32_t seg = (nsb + nblocks - 1) / nblocks;
-  const uint32_t a = min(nsb, blockIdx.x * seg), e = min(nsb, a + seg);
-  {
-    uint64_t part = 0;
-    for (uint32_t i = a + threadIdx.x; i < e; i += blockDim.x) part += B.hist[i];
-    for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if ((threadIdx.x & 31) == 0) s_scan[threadIdx.x >> 5] = part;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      uint64_t t = 0;
-      for (int i = 0; i < B_THREADS / 32; ++i) t += s_scan[i];
-      B.partial[blockIdx.x] = t;
-    }
-  }
-  grid_barrier(B, nblocks);
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    uint64_t run = 0;
-    for (uint32_t c = 0; c < nblocks; ++c) {
-      const uint64_t v = B.partial[c];
-      B.partial[c] = run;
-      run += v;
-    }
-  }
-  grid_barrier(B, nblocks);
-  {  // block-wide scan of this CTA's segment, blockDim values per step
-    uint64_t run = B.partial[blockIdx.x];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (uint32_t base = a; base < e; base += blockDim.x) {
-      const uint32_t i = base + threadIdx.x;
-      const uint64_t v = i < e ? B.hist[i] : 0;
-      uint64_t incl = v;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint64_t t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-      }
-      if (lane == 31) s_scan[warp] = incl;
-      __syncthreads();
-      uint64_t wbase = 0, total = 0;
-      for (int k = 0; k < B_THREADS / 32; ++k) {
-        if (k < warp) wbase += s_scan[k];
-        total += s_scan[k];
-      }
-      if (i < e) B.off[i] = run + wbase + incl - v;
-      run += total;
-      __syncthreads();
-    }
-  }
-  grid_barrier(B, nblocks);
-
-  // ---- phase 2: scatter by global superbin (queue slots include holes)
-  const uint32_t n_slots = *(volatile uint32_t*)(B.ctr + 0);
+  const uint32_t n_slots = *(volatile uint32_t*)(B.ctr + 0);  // queue entries, holes included
   const uint32_t n_res = *(volatile uint32_t*)(B.ctr + 5);
-  scatter_by_superbin(B.queue, n_slots, B.off, B.cursor, B.binned, blockIdx.x * blockDim.x + threadIdx.x,
-                      nblocks * blockDim.x);
-  grid_barrier(B, nblocks);
+  if (STAGED) {  // binning: only the staged crossing phase needs chunks sorted by superbin
+    // ---- phase 1: exclusive scan of hist[0, n_sb_total) over all CTAs
+    const uint32_t nsb = H.n_sb_total;
+    const uint32_t seg = (nsb + nblocks - 1) / nblocks;
+    const uint32_t a = min(nsb, blockIdx.x * seg), e = min(nsb, a + seg);
+    {
+      uint64_t part = 0;
+      for (uint32_t i = a + threadIdx.x; i < e; i += blockDim.x) part += B.hist[i];
+      for (int o = 16; o; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+      if ((threadIdx.x & 31) == 0) s_scan[threadIdx.x >> 5] = part;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        uint64_t t = 0;
+        for (int i = 0; i < B_THREADS / 32; ++i) t += s_scan[i];
+        B.partial[blockIdx.x] = t;
+      }
+    }
+    grid_barrier(B, nblocks);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      uint64_t run = 0;
+      for (uint32_t c = 0; c < nblocks; ++c) {
+        const uint64_t v = B.partial[c];
+        B.partial[c] = run;
+        run += v;
+      }
+    }
+    grid_barrier(B, nblocks);
+    {  // block-wide scan of this CTA's segment, blockDim values per step
+      uint64_t run = B.partial[blockIdx.x];
+      const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+      for (uint32_t base = a; base < e; base += blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        const uint64_t v = i < e ? B.hist[i] : 0;
+        uint64_t incl = v;
+  #pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_scan[warp] = incl;
+        __syncthreads();
+        uint64_t wbase = 0, total = 0;
+        for (int k = 0; k < B_THREADS / 32; ++k) {
+          if (k < warp) wbase += s_scan[k];
+          total += s_scan[k];
+        }
+        if (i < e) B.off[i] = run + wbase + incl - v;
+        run += total;
+        __syncthreads();
+      }
+    }
+    grid_barrier(B, nblocks);
 
-  // ---- phase 3: crossing tests, chunks of ppc binned points
+    // ---- phase 2: scatter by global superbin (queue slots include holes)
+    scatter_by_superbin(B.queue, n_slots, B.off, B.cursor, B.binned, blockIdx.x * blockDim.x + threadIdx.x,
+                        nblocks * blockDim.x);
+    grid_barrier(B, nblocks);
+  }
+
+  // ---- phase 3: crossing tests, chunks of ppc binned points (staged), or
+  // of the residual queue in arrival order, its unused entries skipped
+  const Residual* __restrict__ cross_in = STAGED ? B.binned : B.queue;
+  const uint32_t n_cross = STAGED ? n_res : n_slots;
   const uint32_t ppc = H.ppc;
-  const uint32_t n_items = (n_res + ppc - 1) / ppc;
+  const uint32_t n_items = (n_cross + ppc - 1) / ppc;
   const BatchStore store{B.tiles, B.queries};
   uint32_t phase = 0;
   while (true) {
@@ -396,7 +405,7 @@ __global__ void __launch_bounds__(B_THREADS, 3) k_batch(PlanBufs B) {
       staged = stage_mem;
     }
     const uint32_t first = w * ppc;
-    batch_test_chunk(s_sets, H.n_sets, B.binned, first, min(ppc, n_res - first), staged, s_region,
+    batch_test_chunk(s_sets, H.n_sets, cross_in, first, min(ppc, n_cross - first), staged, s_region,
                      store);
     __syncthreads();
   }
@@ -493,7 +502,7 @@ static pip_status plan_capture(pip_plan_s* P, int t, cudaStream_t s) {
   if (e == cudaSuccess) {
     cudaMemcpyAsync(P->tables.p, P->host_tables[t], P->tables_bytes, cudaMemcpyHostToDevice, cs);
     cudaMemsetAsync(P->ctr.p, 0, 8 * sizeof(uint32_t), cs);
-    cudaMemsetAsync(P->hist.p, 0, (2 * P->sb_cap + 2) * sizeof(uint32_t), cs);
+    if (P->staged) cudaMemsetAsync(P->hist.p, 0, (2 * P->sb_cap + 2) * sizeof(uint32_t), cs);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)P->grid);
     cfg.blockDim = dim3(B_THREADS);

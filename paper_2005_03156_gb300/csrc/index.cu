@@ -1119,6 +1119,7 @@ static void resolve_opts(const pip_build_opts& in, int64_t n_poly, long long w, 
   if (o.compact_edges > COMPACT_MAX_EDGES) o.compact_edges = COMPACT_MAX_EDGES;
   if (o.approx_units > 0 || n_poly > (int64_t)CAND_ID_MASK + 1) o.compact_edges = -1;
   o.compact_early = (o.compact_edges > 0 && o.compact_early > 0) ? 1 : 0;
+  o.bin_residual = o.bin_residual > 0 ? 1 : o.bin_residual < 0 ? -1 : 0;
 }
 
 // Build the hierarchy arrays on the device.

@@ -506,11 +506,12 @@ __device__ __forceinline__ void test_warp_slice(const IndexView& ix, const Resid
                                                 uint32_t first, uint32_t count, const uint4* staged,
                                                 uint32_t region16, Store store) {
   const int lane = threadIdx.x & 31;
-  const bool active = (uint32_t)lane < count;
+  bool active = (uint32_t)lane < count;
   Residual r = make_uint4(0, 0, 0, 0);
   const uint4* bp = ix.blobs;
+  if (active) r = binned[first + lane];
+  active &= r.w != RES_HOLE;  // a queue read in arrival order keeps its unused reserved entries
   if (active) {
-    r = binned[first + lane];
     const uint32_t off = ix.slot_off[r.w];
     bp = staged ? staged + (off - region16) : ix.blobs + off;
   }

@@ -453,6 +453,15 @@ cudaError_t k1_launch_lockstep(const IndexView& ix, const double* lon, const dou
   return cudaGetLastError();
 }
 
+// Binning the residual by superbin before the unstaged crossing test did not
+// pay at any density measured (state workload, 1e8 points, split ratios 128
+// / 48 / 16 / 8, i.e. 0.44 / 2.8 / 24 / 75 residual points per superbin:
+// the test over the queue in arrival order took 0.141 / 0.295 / 0.733 /
+// 1.162 ms against 0.206 / 0.361 / 0.770 / 1.251 ms for binning + test).
+// Each point reads its own leaf record either way; the binning's scan and
+// scatter cost more than the locality they buy. So the plain path bins only
+// when asked to or when the staged crossing kernel needs it.
+
 // Scratch of one device-resident projection of n points.
 struct ProjScratch {
   DBuf<Residual> queue, binned;
@@ -471,9 +480,12 @@ pip_status project_device(pip_set_s* S, const double* lon, const double* lat, in
   const IndexView& ix = S->view;
   const int64_t n_sb = std::max<int64_t>(1, ix.n_sb);
   const uint32_t ppc = (uint32_t)std::max(1, S->opts.pts_per_cta);
+  // binning by superbin: when asked for, or for the staged crossing kernel,
+  // which needs each chunk's records contiguous
+  const bool bin = S->opts.stage_depth > 0 || S->opts.bin_residual > 0;
   ProjScratch w;
-  if (!w.queue.alloc(al, k1_queue_entries(n), s) || !w.binned.alloc(al, n, s) || !w.hist.alloc(al, 2 * n_sb, s) ||
-      !w.off.alloc(al, n_sb, s) || !w.ctr.alloc(al, 4, s))
+  if (!w.queue.alloc(al, k1_queue_entries(n), s) || (bin && !w.binned.alloc(al, n, s)) ||
+      !w.hist.alloc(al, 2 * n_sb, s) || !w.off.alloc(al, n_sb, s) || !w.ctr.alloc(al, 4, s))
     return fail(PIP_ENOMEM, "pip_project: scratch allocation failed");
   uint32_t* hist = w.hist.p;
   uint32_t* cursor = w.hist.p + n_sb;
@@ -486,15 +498,21 @@ pip_status project_device(pip_set_s* S, const double* lon, const double* lat, in
   PIP_CUDA(cudaMemsetAsync(w.ctr.p, 0, 4 * sizeof(uint32_t), s));
   PIP_CUDA(k1_launch(ix, lon, lat, n, out, w.queue.p, w.ctr.p, hist, s));
   if (prof >= 0) PIP_CUDA(cudaEventRecord(S->prof_ev[4 * prof + 1], s));
-  pip_status st = scan_u32_to_u64(*al, hist, w.off.p, n_sb, nullptr, s);
-  if (st != PIP_OK) return st;
-  k_scatter<<<(unsigned)(num_sms() * 8), 256, 0, s>>>(w.queue.p, w.ctr.p, w.off.p, cursor, w.binned.p);
-  PIP_CUDA(cudaGetLastError());
+  pip_status st = PIP_OK;
+  if (bin) {
+    st = scan_u32_to_u64(*al, hist, w.off.p, n_sb, nullptr, s);
+    if (st != PIP_OK) return st;
+    k_scatter<<<(unsigned)(num_sms() * 8), 256, 0, s>>>(w.queue.p, w.ctr.p, w.off.p, cursor, w.binned.p);
+    PIP_CUDA(cudaGetLastError());
+  }
   if (prof >= 0) PIP_CUDA(cudaEventRecord(S->prof_ev[4 * prof + 2], s));
-  st = k3_launch(ix, S->opts.stage_depth, w.binned.p, w.ctr.p + 2, ppc, w.ctr.p + 1, out, S->status.p, s);
+  // K3 over the binned points, or over the whole queue in arrival order
+  // (its unused reserved entries are skipped)
+  st = bin ? k3_launch(ix, S->opts.stage_depth, w.binned.p, w.ctr.p + 2, ppc, w.ctr.p + 1, out, S->status.p, s)
+           : k3_launch(ix, -1, w.queue.p, w.ctr.p + 0, ppc, w.ctr.p + 1, out, S->status.p, s);
   if (st != PIP_OK) return st;
   if (prof >= 0) PIP_CUDA(cudaEventRecord(S->prof_ev[4 * prof + 3], s));
-  count_launches(3);  // K1, scatter, K3 (the scan counts its own)
+  count_launches(bin ? 3 : 2);  // K1, scatter, K3 (the scan counts its own)
   if (stats) {
     uint32_t c[3];
     PIP_CUDA(cudaMemcpyAsync(c, w.ctr.p, sizeof(c), cudaMemcpyDeviceToHost, s));

@@ -100,7 +100,24 @@ OPTION_CASES = [
     dict(compact_edges=3, max_depth=-1, cell_log2=15),   # uniform grid of compact cells
     dict(compact_edges=1, compact_early=1),              # compact cells stop splitting (one edge)
     dict(compact_edges=3, compact_early=1, size_ratio=16),  # ... and up to three edges, shallow
+    dict(bin_residual=1),                                # residual binned by superbin
+    dict(bin_residual=-1, leaf_edges=2, size_ratio=8),   # residual tested in arrival order (holes skipped)
 ]
+
+
+def test_binned_and_arrival_order_crossing_tests_agree(pipm, tiny_set_holes):
+    """The crossing kernel over the binned residual (bin_residual = 1) and over
+    the queue in arrival order (the default) give the oracle's ids, at a
+    residual density of many points per superbin."""
+    ps = tiny_set_holes
+    lon, lat = configs.tiny_points(ps, n=200_000, seed=27)
+    want = oracle.join_hier(ps, lon, lat)
+    for b in (1, 0):
+        s = pipm.load_polygon_set(ps, opts=dict(leaf_edges=1000, size_ratio=-1, max_depth=-1, cell_log2=16,
+                                                bin_residual=b))
+        got, stats = pipm.pip_project_ex(s, torch.from_numpy(lon).cuda(), torch.from_numpy(lat).cuda())
+        assert (got.cpu().numpy() == want).all(), b
+        assert stats["residual"] >= 8 * s.info()["superbins"]
 
 
 @pytest.mark.parametrize("opts", OPTION_CASES, ids=[str(o) for o in OPTION_CASES])
