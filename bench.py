@@ -739,8 +739,11 @@ def run_national(args):
     clocks.start()
     t = time.perf_counter()
     steps = max(1, args.steps)
+    step_ms = []
     for _ in range(steps):
+        t1 = time.perf_counter()
         pipm.pip_project(s, lon_h, lat_h, out_h)
+        step_ms.append((time.perf_counter() - t1) * 1e3)
     dt = (time.perf_counter() - t) / steps
     clk = clocks.stop()
     # device-resident time of one chunk, by stage (what the stream hides behind the copies)
@@ -773,6 +776,7 @@ def run_national(args):
                    "generation_s": {"set": gen_set, "points": gen_pts}},
         "h2d_gbs": h2d_gbs, "bound_pts_s": bound, "frac_of_bound": (n / dt) / bound,
         "sampled_parity_100k": ok, "clocks": clk, "device_chunk_stages_ms": chunk_stages,
+        "step_ms": {"min": min(step_ms), "median": float(np.median(step_ms)), "max": max(step_ms)},
     }
     print(json.dumps(line))
 

@@ -204,7 +204,11 @@ pip_status pip_set_free(pip_set set);
 /* out[i] = id((lon[i], lat[i])) for i < n. Asynchronous on `stream` when
  * lon, lat and out are device pointers. With host pointers the call streams
  * the points through the device in chunks (pinned host memory overlaps the
- * copies with compute) and returns after out[] is written.
+ * copies with compute) and returns after out[] is written. The set's first
+ * host-memory call reserves its staging (a second stream, two 16M-point
+ * chunk buffers and their scratch: about 1.2 GB of device memory, plus the
+ * per-superbin counts), kept until pip_set_free; host-memory calls on one
+ * set run one at a time.
  * out must not alias lon or lat. When device-resident, n must stay about
  * 1M below 2^32 per call (the residual queue is indexed with 32 bits and
  * holds n plus two reserved chunks per warp); larger n gives PIP_EINVAL. */

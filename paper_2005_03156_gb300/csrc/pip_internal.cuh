@@ -436,6 +436,10 @@ pip_status scan_u32_to_u64_scratch(const uint32_t* in, uint64_t* out, int64_t n,
 }  // namespace pip
 
 // The set as the library holds it.
+namespace pip {
+struct HostStage;  // host.cu
+}
+
 struct pip_set_s {
   int device = 0;
   pip::Alloc alloc;
@@ -460,7 +464,31 @@ struct pip_set_s {
   // per-stage profiling: 4 events per recorded call
   std::vector<cudaEvent_t> prof_ev;
   int32_t prof_cap = 0, prof_n = 0;
-  ~pip_set_s() {
-    for (cudaEvent_t e : prof_ev) cudaEventDestroy(e);
-  }
+  // host-memory calls: a second stream, staging buffers and projection
+  // scratch, reserved at the first call and reused (no allocation per call)
+  pip::HostStage* host = nullptr;
+  ~pip_set_s();
 };
+
+namespace pip {
+// Scratch of device-resident projections of up to `cap` points: residual
+// queue, binned residual (when binning), per-superbin counts and cursors,
+// offsets, counters. The host-memory form reserves one per stream and
+// reuses it for every chunk.
+struct ProjScratch {
+  DBuf<Residual> queue, binned;
+  DBuf<uint32_t> hist;   // [n_sb] counts then [n_sb] cursors
+  DBuf<uint64_t> off;    // [n_sb] exclusive scan of the counts
+  DBuf<uint32_t> ctr;    // [0] queue count, [1] crossing work items, [2] residual count
+  int64_t cap = 0;       // points
+  int64_t n_sb = 0;      // superbins of the index it was sized for
+  bool bin = false;      // holds the binned buffer
+};
+pip_status proj_scratch_alloc(pip_set_s* S, ProjScratch& w, int64_t n, cudaStream_t s);
+bool proj_scratch_fits(const pip_set_s* S, const ProjScratch& w, int64_t n);
+// Staging of the host-memory form, kept with the set (host.cu).
+HostStage* host_stage_new();
+void host_stage_free(HostStage* h);
+pip_status project_device_with(pip_set_s* S, const double* lon, const double* lat, int64_t n, int32_t* out,
+                               cudaStream_t s, pip_project_stats* stats, ProjScratch* pre);
+}  // namespace pip

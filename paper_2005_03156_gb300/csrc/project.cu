@@ -462,16 +462,37 @@ cudaError_t k1_launch_lockstep(const IndexView& ix, const double* lon, const dou
 // scatter cost more than the locality they buy. So the plain path bins only
 // when asked to or when the staged crossing kernel needs it.
 
-// Scratch of one device-resident projection of n points.
-struct ProjScratch {
-  DBuf<Residual> queue, binned;
-  DBuf<uint32_t> hist;   // [n_sb] counts then [n_sb] cursors
-  DBuf<uint64_t> off;    // [n_sb] exclusive scan of the counts
-  DBuf<uint32_t> ctr;    // [0] queue count, [1] chunk counter
-};
+
+// Binning by superbin: when asked for, or for the staged crossing kernel,
+// which needs each chunk's records contiguous.
+static bool bins_residual(const pip_set_s* S) { return S->opts.stage_depth > 0 || S->opts.bin_residual > 0; }
+
+pip_status proj_scratch_alloc(pip_set_s* S, ProjScratch& w, int64_t n, cudaStream_t s) {
+  Alloc* al = &S->alloc;
+  const int64_t n_sb = std::max<int64_t>(1, S->view.n_sb);
+  const bool bin = bins_residual(S);
+  w.cap = 0;
+  w.binned.release();
+  if (!w.queue.alloc(al, k1_queue_entries(n), s) || (bin && !w.binned.alloc(al, n, s)) ||
+      !w.hist.alloc(al, 2 * n_sb, s) || !w.off.alloc(al, n_sb, s) || !w.ctr.alloc(al, 4, s))
+    return fail(PIP_ENOMEM, "pip_project: scratch allocation failed");
+  w.cap = n;
+  w.n_sb = n_sb;
+  w.bin = bin;
+  return PIP_OK;
+}
+
+bool proj_scratch_fits(const pip_set_s* S, const ProjScratch& w, int64_t n) {
+  return w.cap >= n && w.n_sb == std::max<int64_t>(1, S->view.n_sb) && (w.bin || !bins_residual(S));
+}
 
 pip_status project_device(pip_set_s* S, const double* lon, const double* lat, int64_t n, int32_t* out,
                           cudaStream_t s, pip_project_stats* stats) {
+  return project_device_with(S, lon, lat, n, out, s, stats, nullptr);
+}
+
+pip_status project_device_with(pip_set_s* S, const double* lon, const double* lat, int64_t n, int32_t* out,
+                               cudaStream_t s, pip_project_stats* stats, ProjScratch* pre) {
   if (n <= 0) return PIP_OK;
   if (n >= (1ll << 32) - 1 || k1_queue_entries(n) >= (1ll << 32))
     return fail(PIP_EINVAL, "pip_project: too many points for one device call (queue indices are 32-bit)");
@@ -480,13 +501,14 @@ pip_status project_device(pip_set_s* S, const double* lon, const double* lat, in
   const IndexView& ix = S->view;
   const int64_t n_sb = std::max<int64_t>(1, ix.n_sb);
   const uint32_t ppc = (uint32_t)std::max(1, S->opts.pts_per_cta);
-  // binning by superbin: when asked for, or for the staged crossing kernel,
-  // which needs each chunk's records contiguous
-  const bool bin = S->opts.stage_depth > 0 || S->opts.bin_residual > 0;
-  ProjScratch w;
-  if (!w.queue.alloc(al, k1_queue_entries(n), s) || (bin && !w.binned.alloc(al, n, s)) ||
-      !w.hist.alloc(al, 2 * n_sb, s) || !w.off.alloc(al, n_sb, s) || !w.ctr.alloc(al, 4, s))
-    return fail(PIP_ENOMEM, "pip_project: scratch allocation failed");
+  const bool bin = bins_residual(S);
+  ProjScratch own;
+  if (!pre || !proj_scratch_fits(S, *pre, n)) {
+    pip_status a = proj_scratch_alloc(S, own, n, s);
+    if (a != PIP_OK) return a;
+    pre = &own;
+  }
+  ProjScratch& w = *pre;
   uint32_t* hist = w.hist.p;
   uint32_t* cursor = w.hist.p + n_sb;
   int prof = -1;

@@ -50,6 +50,7 @@ static pip_status load_common(const V* vx, const V* vy, int64_t n_vert, const in
   cudaStream_t s = (cudaStream_t)stream;
   std::unique_ptr<pip_set_s> S(new pip_set_s());
   PIP_CUDA(cudaGetDevice(&S->device));
+  S->host = host_stage_new();
   if (alloc) {
     S->alloc.hook = *alloc;
     S->alloc.has_hook = true;
