@@ -777,6 +777,7 @@ def run_national(args):
         "h2d_gbs": h2d_gbs, "bound_pts_s": bound, "frac_of_bound": (n / dt) / bound,
         "sampled_parity_100k": ok, "clocks": clk, "device_chunk_stages_ms": chunk_stages,
         "step_ms": {"min": min(step_ms), "median": float(np.median(step_ms)), "max": max(step_ms)},
+        "median_step_pts_s": n / (float(np.median(step_ms)) / 1e3),
     }
     print(json.dumps(line))
 
