@@ -152,9 +152,13 @@ extern "C" pip_status pip_set_info(pip_set set, pip_set_info_t* info) {
 
 extern "C" pip_status pip_set_free(pip_set set) {
   if (!set) return PIP_OK;
+  int cur = 0;  // free on the set's own device (its streams and pool live there)
+  cudaGetDevice(&cur);
+  if (cur != set->device) cudaSetDevice(set->device);
   cudaDeviceSynchronize();
   delete set;
   cudaDeviceSynchronize();
+  if (cur != set->device) cudaSetDevice(cur);
   return PIP_OK;
 }
 
