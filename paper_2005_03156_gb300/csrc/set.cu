@@ -153,12 +153,13 @@ extern "C" pip_status pip_set_info(pip_set set, pip_set_info_t* info) {
 extern "C" pip_status pip_set_free(pip_set set) {
   if (!set) return PIP_OK;
   int cur = 0;  // free on the set's own device (its streams and pool live there)
+  const int dev = set->device;
   cudaGetDevice(&cur);
-  if (cur != set->device) cudaSetDevice(set->device);
+  if (cur != dev) cudaSetDevice(dev);
   cudaDeviceSynchronize();
   delete set;
   cudaDeviceSynchronize();
-  if (cur != set->device) cudaSetDevice(cur);
+  if (cur != dev) cudaSetDevice(cur);
   return PIP_OK;
 }
 
