@@ -80,7 +80,7 @@ typedef struct {
   int32_t max_depth;    /* subdivision levels below the top grid (0 = auto, < 0 = none:
                            a uniform grid) */
   int32_t fanout_log2;  /* reported only: a split cell always has 4 x 4 children, held
-                           in one 32-byte trie node */
+                           in one 16-byte trie entry (32-byte node with compact leaves) */
   int32_t leaf_edges;   /* split a boundary cell holding more kept edges than this (0 = auto) */
   int32_t size_ratio;   /* split while cell side * ratio > smallest candidate box side
                            (0 = auto: 128, or 48 with compact leaves or the approximate mode;
